@@ -1,0 +1,313 @@
+"""Benchmark of the TNEP tensor path on bulk water (one JSON line on rank 0).
+
+Workload: 13,824 H2O (41,472 atoms) in a 74.5 A periodic cube, a 2,000-frame
+random walk (0.01 A per atom per step); per frame the dipole (rank 1) and
+polarizability (rank 2) of two random TNEP models (rc_R = 6 A, rc_A = 4 A,
+n_max 4/4, basis 8/8, l_max 4 + 4-body, 30 hidden units, 2 types), then the
+IR and Raman (iso, aniso) spectra of the 2,000-frame series (dt = 1 fs).
+One step = the whole path over the whole trajectory.
+
+value: atom-frames/s with positions resident in HBM (1.0 GB, larger than L2)
+e2e:   the same through the public API with pinned host inputs and host outputs
+--impl reference: the FP64 CPU oracle on the host cores, bounded samples.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RC = (6.0, 4.0)
+N_SIDE, L_BOX = 24, 74.5
+DT_FS = 1.0
+METRIC = "TNEP atom-frames/s served vs plain at rel err <=1e-4 vs FP64; p50/p99 latency"
+# Algorithmic flop model per atom and model evaluation (forward + backward):
+# radial pair 235, angular pair 1380, per atom 4500 (descriptor products and
+# the 30x30 network forward and backward).
+PHI_R, PHI_A, PHI_ATOM = 235.0, 1380.0, 4500.0
+SMS, FP32_LANES = 152, 128
+
+
+def workload_config(n_frames):
+    return {
+        "workload": f"bulk water 13,824 H2O (41,472 atoms), 74.5 A periodic cube, {n_frames}-frame random walk; "
+                    "dipole (rank 1) + polarizability (rank 2) TNEP models; IR + Raman iso/aniso spectra",
+        "atoms": N_SIDE ** 3 * 3,
+        "frames": n_frames,
+        "models": "rank1 + rank2, n_max 4/4, basis 8/8, l_max 4 + 4-body, H=30, rc 6/4 A",
+        "l2": "inputs larger than L2 (positions 1.0 GB resident, no flush needed)",
+    }
+
+
+def make_models(tn, synth):
+    rng = np.random.default_rng(synth.seed_for(2, 1))
+    out, hps, params = [], [], []
+    for rank in (1, 2):
+        hp = synth.HyperParams(n_types=2, rank=rank)
+        p = synth.model_params(hp, rng)
+        out.append(tn.Model.from_hyper(hp, p, synth.default_q_scaler(hp)) if tn else None)
+        hps.append(hp)
+        params.append(p)
+    return out, hps, params
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(hps, params, frame, box, types, n_centers, seed=0):
+    """Times the FP64 oracle (both models) on n_centers atoms of one frame."""
+    import torch
+    import oracle
+    import synth
+    oms = [oracle.OracleModel.from_flat(hp, p, synth.default_q_scaler(hp), *RC) for hp, p in zip(hps, params)]
+    centers = np.random.default_rng(seed).choice(len(types), size=n_centers, replace=False)
+    t0 = time.perf_counter()
+    for om in oms:
+        oracle.evaluate(om, frame, box, types, centers=centers)
+    dt = time.perf_counter() - t0
+    return dt, torch.get_num_threads()
+
+
+def run_reference(args, rank, world):
+    """FP64 CPU oracle arm: bounded samples of the same workload."""
+    import synth
+    if rank != 0:
+        return 0
+    frames, types, box = synth.water_bulk(n_frames=max(args.warmup + args.steps, 1))
+    _, hps, params = make_models(None, synth)
+    n_c = args.ref_centers
+    for w in range(args.warmup):
+        oracle_sample(hps, params, frames[w], box, types, max(8, n_c // 8), seed=w)
+    times, cores = [], 1
+    for k in range(args.steps):
+        dt, cores = oracle_sample(hps, params, frames[args.warmup + k], box, types, n_c, seed=100 + k)
+        times.append(dt)
+    t = float(np.mean(times))
+    value = n_c / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "atom-frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.frames),
+        "cpu_baseline": {"value": value, "unit": "atom-frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n_c} atoms of one frame per step, both models"},
+        "e2e": {"value": value, "unit": "atom-frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--frames", type=int, default=2000)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-centers", type=int, default=400)
+    ap.add_argument("--cpu-centers", type=int, default=1500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as g
+    import synth
+
+    g.build()
+    from paper_2312_05233_gb300 import tnep as tn
+
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # each rank evaluates its own trajectory shard (weak scaling over frames)
+    frames, types, box = synth.water_bulk(n_frames=args.frames)
+    if rank:
+        frames = frames[::-1].copy()
+    F, N = frames.shape[0], frames.shape[1]
+    models, hps, params = make_models(tn, synth)
+    ctx = tn.tnep_create(models, 2, RC, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+
+    pos_d = torch.from_numpy(frames).to(dev)
+    box_all = np.ascontiguousarray(np.broadcast_to(box, (F, 3)), dtype=np.float32)
+    box_d = torch.from_numpy(box_all).to(dev)
+    types_d = torch.from_numpy(types).to(dev)
+    out_d = torch.empty(F * 12, dtype=torch.float64, device=dev)
+    pos_h = torch.from_numpy(frames).pin_memory()
+    box_h = torch.from_numpy(box_all).pin_memory()
+    types_h = torch.from_numpy(types).pin_memory()
+    out_h = torch.empty(F * 12, dtype=torch.float64).pin_memory()
+    M = F // 2
+
+    def step_device():
+        tn.tnep_eval(ctx, pos_d, box_d, types_d, out=out_d, stream=sp)
+        mu = out_d[:F * 3].view(F, 3)
+        al = out_d[F * 3:].view(F, 9)
+        tn.tnep_spectrum(mu, DT_FS, tn.TNEP_SPECTRUM_IR, M, stream=sp)
+        tn.tnep_spectrum(al, DT_FS, tn.TNEP_SPECTRUM_RAMAN_ISO, M, stream=sp)
+        tn.tnep_spectrum(al, DT_FS, tn.TNEP_SPECTRUM_RAMAN_ANISO, M, stream=sp)
+
+    def step_e2e():
+        tn.tnep_eval(ctx, pos_h, box_h, types_h, out=out_h, stream=sp)
+        mu = out_h[:F * 3].view(F, 3)
+        al = out_h[F * 3:].view(F, 9)
+        tn.tnep_spectrum(mu, DT_FS, tn.TNEP_SPECTRUM_IR, M, stream=sp)
+        tn.tnep_spectrum(al, DT_FS, tn.TNEP_SPECTRUM_RAMAN_ISO, M, stream=sp)
+        tn.tnep_spectrum(al, DT_FS, tn.TNEP_SPECTRUM_RAMAN_ANISO, M, stream=sp)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fused_ms, nbr_ms, fused_launches = 0.0, 0.0, 0
+    l0 = tn.tnep_get_option(ctx, tn.TNEP_OPT_KERNEL_LAUNCHES_TOTAL)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+            fused_ms += tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_KERNEL_MS)
+            nbr_ms += tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_NBR_MS)
+            fused_launches += int(tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_KERNEL_LAUNCHES))
+        ev1.record(stream)
+        barrier()
+    launches = tn.tnep_get_option(ctx, tn.TNEP_OPT_KERNEL_LAUNCHES_TOTAL) - l0
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+
+    # end to end through the public API with pinned host buffers
+    for _ in range(1):
+        step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+
+    # neighbour statistics of the last frame for the flop model
+    offs = np.array([0, N])
+    cR, cA, _, _ = tn.tnep_neighbors(ctx, offs, frames[-1], box[None], cap_R=1, cap_A=1)
+    nn_R, nn_A = float(cR.mean()), float(cA.mean())
+    flops_atom = nn_R * PHI_R + nn_A * PHI_A + PHI_ATOM
+    atom_evals = F * N * 2 * args.steps
+    achieved_tflops = flops_atom * atom_evals / (fused_ms * 1e-3) / 1e12 if fused_ms > 0 else None
+    clocks = clk.summary()
+    peak_tflops = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+
+    units = F * N * world
+    value = units / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "atom-frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F),
+        "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "atom-frames/s",
+                "h2d_bytes_per_step": int(F * N * 12 + F * 12 + N * 4),
+                "d2h_bytes_per_step": int(F * 12 * 8 + 3 * 2 * (M + 1) * 8), "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches / args.steps),
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None, "traffic": None,
+                     "kernel": "k_fused (descriptor + network + partial force + contraction)",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
+                     "flops_per_atom_eval": flops_atom, "nn_R": nn_R, "nn_A": nn_A,
+                     "fused_ms_per_step": fused_ms / args.steps, "nbr_ms_per_step": nbr_ms / args.steps,
+                     "fused_launches_per_step": fused_launches / args.steps},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, cores = oracle_sample(hps, params, frames[0], box, types, args.cpu_centers)
+        line["cpu_baseline"] = {"value": args.cpu_centers / dt, "unit": "atom-frames/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_centers} atoms of frame 0, both models, FP64 oracle"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * tnep.h -- C ABI of the GB300 (sm_103a) TNEP tensor library.
+ *
+ * TNEP (arXiv 2312.05233) predicts the dipole mu (rank 1, Eq. 3) and the
+ * polarizability / susceptibility alpha (rank 2, Eq. 4) of a structure from
+ * the derivative of a neuroevolution-potential "site value" U_i with respect
+ * to the pair vectors r_ij = r_j - r_i (Sec. II.A, the partial force):
+ *
+ *   mu          = - sum_i sum_{j != i} |r_ij|^2 dU_i/dr_ij                  (Eq. 3)
+ *   alpha^{uv}  =   sum_i U_i delta^{uv} - sum_i sum_{j != i} r_ij^u dU_i/dr_ij^v   (Eq. 4)
+ *
+ * U_i = NN(q_i) is a single-hidden-layer tanh network (Eq. 1) of the NEP
+ * descriptor q_i.  The paper defers q_i to the NEP papers; this library uses
+ * the published NEP form:
+ *   f_c(r)  = (1 + cos(pi r / rc)) / 2 for r < rc,  x = 2 (r/rc - 1)^2 - 1,
+ *   f_k(r)  = (T_k(x) + 1) f_c(r) / 2,  k = 0..basis   (Chebyshev T_k),
+ *   g_n(r)  = sum_k c^{t_i t_j}_{nk} f_k(r)   (separate c for radial/angular),
+ *   radial  q_n  = sum_{r_ij < rc_R} g^R_n(r_ij),              n = 0..n_max_R
+ *   angular q_nl = sum_{j,k} g^A_n(r_ij) g^A_n(r_ik) P_l(cos theta_ijk), l = 1..l_max
+ *   4-body  q_n  = sum_{m1+m2+m3=0} (2 2 2; m1 m2 m3) A_n2m1 A_n2m2 A_n2m3,
+ *           A_nlm = sum_{r_ij < rc_A} g^A_n(r_ij) Y_lm(r_ij / r_ij)
+ *   U_i     = sum_mu w1_mu tanh(sum_nu W0_mu,nu s_nu - b0_mu) - b1,  s = q * q_scaler.
+ *
+ * The IR and Raman spectra are cosine transforms of the time-origin averaged
+ * autocorrelation of mu(t) (Sec. II.F, Eqs. 5-6) and of gamma = Tr(alpha)/3
+ * and beta = alpha - gamma I (Sec. II.G, Eqs. 7-9).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a tnep_status; nothing throws across the ABI.
+ *     tnep_last_error() gives a thread-local message for the last failure.
+ *   - Positions are float32 Angstrom, [n][3] row-major.  Boxes are
+ *     orthorhombic edge lengths [3]; an edge of 0 marks an open
+ *     (non-periodic) axis.  A periodic edge shorter than 2 * rc_R returns
+ *     TNEP_ERR_BOX_TOO_SMALL (minimum image must be unique).
+ *   - Types are int32 in [0, n_types).
+ *   - Input and output pointers may be host or device memory (detected with
+ *     cudaPointerGetAttributes).  Inputs are borrowed for the duration of the
+ *     call and never retained; outputs are owned by the caller.
+ *   - tnep_eval* calls are synchronous: results are in `out` when the call
+ *     returns.  `stream` (a cudaStream_t, or NULL for the context's own
+ *     stream) is the stream the work is ordered on.
+ *   - Tensor outputs are float64.  Rank 1: [3] (x, y, z).  Rank 2: [9]
+ *     row-major, element (u, v) = alpha^{uv}.
+ *   - Pair selection is exact float32: d = p_j - p_i; on a periodic axis
+ *     d = d - L * rint(d * (1/L)); r2 = (dx*dx + dy*dy) + dz*dz with every
+ *     operation rounded separately (no fused multiply-add); a pair is kept
+ *     iff r2 < rc*rc (rounded to float32).  Strict "<" at the cutoff.
+ */
+#ifndef TNEP_H
+#define TNEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNEP_OK = 0,
+  TNEP_ERR_INVALID = 1,            /* bad argument (null pointer, size, type index, layout) */
+  TNEP_ERR_OOM = 2,                /* device or pinned host allocation failed */
+  TNEP_ERR_BOX_TOO_SMALL = 3,      /* periodic edge < 2 rc_R */
+  TNEP_ERR_NEIGHBOR_OVERFLOW = 4,  /* neighbour count above the hard cap (TNEP_OPT_MAX_NEIGHBORS) */
+  TNEP_ERR_CUDA = 5,               /* a CUDA runtime call failed; see tnep_last_error() */
+  TNEP_ERR_TIMEOUT = 6,            /* a bounded wait expired */
+  TNEP_ERR_UNSUPPORTED = 7,        /* hyper-parameters without a compiled kernel variant */
+  TNEP_ERR_BUSY = 8,               /* serving: request not admitted (slots or memory) */
+  TNEP_ERR_NO_DEVICE = 9           /* no CUDA device or not an sm_103 device */
+} tnep_status;
+
+typedef struct tnep_ctx tnep_ctx;  /* opaque, owned by the library */
+
+/* One TNEP model.  All arrays are caller-owned and copied by tnep_create.
+ *
+ * Flat parameter layout (float32), with D = (n_max_R+1) + (n_max_A+1)*(l_max + use_4body)
+ * and H = n_hidden:
+ *   for each network (n_types networks if per_type_nn, else one):
+ *       W0 [H][D] row-major (hidden unit, descriptor component), b0 [H], w1 [H], b1 [1]
+ *   c_R [n_types][n_types][n_max_R+1][basis_R+1]   (centre type, neighbour type, n, k)
+ *   c_A [n_types][n_types][n_max_A+1][basis_A+1]
+ * Descriptor component order: the radial q_n (n = 0..n_max_R); then for
+ * l = 1..l_max the angular q_nl over n = 0..n_max_A; then the 4-body q_n.
+ */
+typedef struct {
+  int rank;           /* 1 = dipole (Eq. 3), 2 = polarizability / susceptibility (Eq. 4) */
+  int n_max_R;        /* radial channels n = 0..n_max_R */
+  int n_max_A;        /* angular channels n = 0..n_max_A */
+  int basis_R;        /* radial Chebyshev basis k = 0..basis_R */
+  int basis_A;        /* angular Chebyshev basis k = 0..basis_A */
+  int l_max;          /* angular orders l = 1..l_max */
+  int use_4body;      /* 1 adds the l = 2 four-body invariant */
+  int n_hidden;       /* H, hidden tanh units (1..64) */
+  int per_type_nn;    /* 1 = one network per centre type, 0 = one shared network */
+  const float* params;
+  size_t n_params;
+  const float* q_scaler;  /* [D] multiplies q before the network, or NULL = ones */
+  int mlp_precision;      /* 0 = FP32, 1 = BF16 tensor-core MLP with FP32 accumulation */
+} tnep_model_desc;
+
+/* Creates a context on `device` holding `n_models` models that share the
+ * cutoffs {rc_R, rc_A} (Angstrom, rc_A <= rc_R) and therefore one neighbour
+ * list per structure.  `type_names` may be NULL.  Supported kernels:
+ * (n_max_R, n_max_A, basis_R, basis_A, l_max, use_4body) in
+ * {(4,4,8,8,4,1), (3,2,6,5,3,1)}; others return TNEP_ERR_UNSUPPORTED.
+ * n_types <= 8.  Returns TNEP_ERR_NO_DEVICE without a usable GPU. */
+tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types,
+                        const char* const* type_names, const float cutoffs[2], int device,
+                        tnep_ctx** out);
+
+/* Frees every resource of the context (NULL is a no-op). */
+void tnep_destroy(tnep_ctx* ctx);
+
+/* Thread-local message describing the last failed call on this thread. */
+const char* tnep_last_error(void);
+
+/* Size of one model's output per structure: 3 (rank 1) or 9 (rank 2); 0 for a bad index. */
+int tnep_output_dim(const tnep_ctx* ctx, int model);
+
+/* Evaluates every model of the context on `n_frames` frames of `n_atoms` atoms
+ * (a trajectory; Sec. II.H "Workflow").
+ *   pos   [n_frames][n_atoms][3]
+ *   box   [n_frames][3] orthorhombic edges (0 = open axis) or NULL = all open
+ *   types [n_atoms], shared by all frames
+ *   out   [n_models][n_frames][C_m] float64, C_m = tnep_output_dim(ctx, m);
+ *         model m's block starts at n_frames * sum_{m' < m} C_m'.
+ * Frames are processed in chunks (TNEP_OPT_FRAMES_PER_BATCH) with host->device
+ * copies of the next chunk overlapped with the current one when `pos` is
+ * host memory (pinned memory copies asynchronously). */
+tnep_status tnep_eval(tnep_ctx* ctx, int n_frames, int n_atoms, const float* pos,
+                      const float* box, const int* types, double* out, void* stream);
+
+/* Evaluates every model on `n_structs` structures of uneven size in one pass.
+ *   atom_offsets [n_structs + 1] (host memory), structure s owns atoms
+ *                [atom_offsets[s], atom_offsets[s+1]); empty structures allowed
+ *   pos [N][3], box [n_structs][3] (0 = open axis) or NULL, types [N]
+ *   out [n_models][n_structs][C_m] float64 (layout as tnep_eval)
+ *   per_atom  NULL, or [n_models][N][C_m] float32 per-atom contributions in
+ *             input order: rank 1: -sum_j |r_ij|^2 dU_i/dr_ij; rank 2:
+ *             U_i I - sum_j r_ij (x) dU_i/dr_ij (row-major).  Summing them
+ *             over a structure gives its tensor. */
+tnep_status tnep_eval_batch(tnep_ctx* ctx, int n_structs, const int* atom_offsets,
+                            const float* pos, const float* box, const int* types,
+                            double* out, float* per_atom, void* stream);
+
+/* Builds the neighbour lists of a batch (the cell-list and pair-selection
+ * steps of the path) and returns them in input atom order for inspection.
+ *   counts_R/counts_A [N]: neighbours within rc_R / rc_A
+ *   list_R [N][cap_R], list_A [N][cap_A]: neighbour indices (batch-global, input
+ *   order), entries beyond the count (or beyond the cap) are left untouched.
+ *   The order inside one atom's list is deterministic but unspecified. */
+tnep_status tnep_neighbors(tnep_ctx* ctx, int n_structs, const int* atom_offsets,
+                           const float* pos, const float* box, int* counts_R, int* counts_A,
+                           int* list_R, int cap_R, int* list_A, int cap_A, void* stream);
+
+/* Population evaluation (the training-time use, Sec. II.D): `n_pop` parameter
+ * vectors of model `model` (same hyper-parameters, params [n_pop][n_params])
+ * on one batch of structures, with neighbour lists built once.
+ *   target [n_structs][C] float64 reference tensors
+ *   rmse   [n_pop] float64: sqrt(mean over structures and components of
+ *          (prediction - target)^2)
+ *   out    NULL or [n_pop][n_structs][C] float64 predictions */
+tnep_status tnep_eval_population(tnep_ctx* ctx, int model, int n_pop, const float* params,
+                                 int n_structs, const int* atom_offsets, const float* pos,
+                                 const float* box, const int* types, const double* target,
+                                 double* rmse, double* out, void* stream);
+
+/* Spectrum kinds for tnep_spectrum. */
+enum {
+  TNEP_SPECTRUM_IR = 0,          /* series [T][3] = mu(t); omega^2 * lineshape (Eq. 6) */
+  TNEP_SPECTRUM_RAMAN_ISO = 1,   /* series [T][9] = alpha(t); gamma = Tr(alpha)/3 (Eq. 9) */
+  TNEP_SPECTRUM_RAMAN_ANISO = 2  /* series [T][9]; Tr[beta(0) beta(t)], beta = alpha - gamma I */
+};
+
+/* Autocorrelation + one-sided cosine transform (Sec. II.F-G), float64:
+ *   C(tau) = 1/(T - tau) sum_{t=0}^{T-1-tau} x(t).x(t+tau)  (IR: one third of the trace)
+ *   S(nu_k) = dt [C(0) + 2 sum_{tau=1}^{M} C(tau) cos(pi k tau / M)],  nu_k = k / (2 M dt)
+ * with M = max_lag (0 < M < T; M <= 0 selects T/2), the series mean removed
+ * first when subtract_mean != 0.
+ *   series   [T][C] (host or device), C = 3 (IR) or 9 (Raman)
+ *   freq_cm1 [M+1] frequencies in cm^-1, spec [M+1] (host or device)
+ *   acf_out  NULL or [M+1] the autocorrelation itself */
+tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int kind,
+                          int max_lag, int subtract_mean, double* freq_cm1, double* spec,
+                          double* acf_out, void* stream);
+
+/* Tunables (tnep_set_option / tnep_get_option). */
+enum {
+  TNEP_OPT_FRAMES_PER_BATCH = 0,    /* frames per device pass in tnep_eval (0 = automatic) */
+  TNEP_OPT_MAX_NEIGHBORS = 1,       /* hard cap on neighbours per atom (default 1024); lists grow up to it */
+  TNEP_OPT_BLOCK_ATOMS = 2,         /* read-only: atoms per CTA of the fused kernel (128) */
+  TNEP_OPT_LAST_KERNEL_MS = 3,      /* read-only: device time of all fused-kernel launches of the last call (ms) */
+  TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2} (default 1) */
+  TNEP_OPT_LAST_KERNEL_LAUNCHES = 5,/* read-only: fused-kernel launches in the last call */
+  TNEP_OPT_LAST_NBR_MS = 6,         /* read-only: device time of the cell/neighbour pipeline in the last call (ms) */
+  TNEP_OPT_KERNEL_LAUNCHES_TOTAL = 7 /* read-only: kernels launched by this library in this process */
+};
+tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
+tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNEP_H */

@@ -1,0 +1,332 @@
+// Cell lists and neighbour lists for batches of structures (periodic or open).
+//
+// The TNEP descriptor only sees atoms inside the cutoffs rc_R and rc_A, with
+// r_ij = r_j - r_i taken under the minimum image (Sec. II.A).  The pipeline
+// per batch is:
+//   plan    one CTA per structure: box checks, bounding box of open axes,
+//           cell grid with edge >= rc_R / cell_div (at most 2n + 8 cells)
+//   scan    exclusive scan of cells per structure
+//   bin     cell of every atom, atomic slot inside the cell
+//   scan    exclusive scan of cell counts
+//   scatter atoms into their cells
+//   sort    one warp per cell orders its atoms by input index (so the whole
+//           pipeline is deterministic) and writes cell-ordered float4
+//           positions with the type in .w
+//   build   one thread per atom scans the stencil cells and writes the
+//           radial (rc_R) and angular (rc_A) lists, warp-tiled.
+// Pair selection follows the exact float32 recipe documented in tnep.h.
+
+#include "tnep_internal.cuh"
+
+namespace tnep {
+
+namespace {
+
+__device__ __forceinline__ void raise_error(DevStatus* st, int code, int s) {
+  if (atomicCAS(&st->error, 0, code) == 0) st->bad_struct = s;
+}
+
+__global__ void k_plan(NbrArgs a) {
+  const int s = blockIdx.x;
+  const int a0 = a.offsets[s], a1 = a.offsets[s + 1];
+  const int n = a1 - a0;
+  float L[3];
+  for (int d = 0; d < 3; ++d) L[d] = a.box ? a.box[3 * s + d] : 0.0f;
+  float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x) {
+    a.atom_struct[g] = s;
+    for (int d = 0; d < 3; ++d) {
+      const float x = a.pos[3 * (size_t)g + d];
+      mn[d] = fminf(mn[d], x);
+      mx[d] = fmaxf(mx[d], x);
+    }
+  }
+  __shared__ float smn[3][32], smx[3][32];
+  for (int d = 0; d < 3; ++d) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+      mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) { smn[d][w] = mn[d]; smx[d][w] = mx[d]; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int d = 0; d < 3; ++d) {
+    mn[d] = smn[d][0]; mx[d] = smx[d][0];
+    for (int k = 1; k < nw; ++k) { mn[d] = fminf(mn[d], smn[d][k]); mx[d] = fmaxf(mx[d], smx[d][k]); }
+  }
+  StructGrid G;
+  StructBox B;
+  const float edge_min = a.rc_R / (float)a.cell_div * (1.0f + 1e-5f);
+  int nc[3];
+  float ext[3];
+  for (int d = 0; d < 3; ++d) {
+    if (L[d] > 0.0f) {
+      if (L[d] < 2.0f * a.rc_R) raise_error(a.status, TNEP_ERR_BOX_TOO_SMALL, s);
+      nc[d] = max(1, (int)floorf(L[d] / edge_min));
+      ext[d] = L[d];
+    } else if (L[d] < 0.0f || isnan(L[d])) {
+      raise_error(a.status, TNEP_ERR_INVALID, s);
+      nc[d] = 1; ext[d] = 0.0f; L[d] = 0.0f;
+    } else {
+      ext[d] = n > 0 ? mx[d] - mn[d] : 0.0f;
+      if (!(ext[d] < 1e30f)) { raise_error(a.status, TNEP_ERR_INVALID, s); ext[d] = 0.0f; }
+      nc[d] = max(1, min(1 << 20, (int)floorf(ext[d] / edge_min) + 1));
+    }
+  }
+  const long long cap = 2LL * n + 8;
+  while ((long long)nc[0] * nc[1] * nc[2] > cap) {
+    int d = 0;
+    if (nc[1] > nc[d]) d = 1;
+    if (nc[2] > nc[d]) d = 2;
+    nc[d] = max(1, (nc[d] + 1) / 2);
+  }
+  for (int d = 0; d < 3; ++d) {
+    G.nc[d] = nc[d];
+    if (L[d] > 0.0f) {
+      G.L[d] = L[d];
+      G.invL[d] = __fdiv_rn(1.0f, L[d]);
+      G.origin[d] = 0.0f;
+      G.cinv[d] = (float)nc[d] / L[d];
+    } else {
+      G.L[d] = 0.0f;
+      G.invL[d] = 0.0f;
+      G.origin[d] = n > 0 ? mn[d] : 0.0f;
+      const float e = fmaxf(edge_min, ext[d] / (float)nc[d] * (1.0f + 1e-6f));
+      G.cinv[d] = 1.0f / e;
+    }
+    B.L[d] = G.L[d];
+    B.invL[d] = G.invL[d];
+  }
+  G.cell_offset = 0;
+  a.grids[s] = G;
+  a.boxes[s] = B;
+  a.struct_cells[s] = nc[0] * nc[1] * nc[2];
+}
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total, one CTA of 1024.
+__device__ void block_exclusive_scan(const int* in, int* out, int n) {
+  __shared__ int warp_sums[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = min(n, tid * per), hi = min(n, lo + per);
+  int local = 0;
+  for (int k = lo; k < hi; ++k) local += in[k];
+  int incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_sums[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    int v = lane < nw ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) warp_sums[lane] = v;
+  }
+  __syncthreads();
+  int run = incl - local + (w > 0 ? warp_sums[w - 1] : 0);
+  for (int k = lo; k < hi; ++k) {
+    const int v = in[k];
+    out[k] = run;
+    run += v;
+  }
+  if (tid == blockDim.x - 1) out[n] = run;
+}
+
+__global__ void k_scan_structs(NbrArgs a) {
+  block_exclusive_scan(a.struct_cells, a.struct_cells, a.n_structs);
+  __syncthreads();
+  for (int s = threadIdx.x; s < a.n_structs; s += blockDim.x) a.grids[s].cell_offset = a.struct_cells[s];
+  if (threadIdx.x == 0 && a.struct_cells[a.n_structs] > a.cells_cap) raise_error(a.status, TNEP_ERR_INVALID, -1);
+}
+
+__device__ __forceinline__ int cell_coord(float x, const StructGrid& G, int d) {
+  float xw;
+  if (G.L[d] > 0.0f) {
+    xw = x - G.L[d] * floorf(x * G.invL[d]);
+  } else {
+    xw = x - G.origin[d];
+  }
+  int c = (int)floorf(xw * G.cinv[d]);
+  return min(max(c, 0), G.nc[d] - 1);
+}
+
+__global__ void k_bin(NbrArgs a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_atoms) return;
+  const int s = a.atom_struct[g];
+  const StructGrid G = a.grids[s];
+  const int c0 = cell_coord(a.pos[3 * (size_t)g + 0], G, 0);
+  const int c1 = cell_coord(a.pos[3 * (size_t)g + 1], G, 1);
+  const int c2 = cell_coord(a.pos[3 * (size_t)g + 2], G, 2);
+  const int cell = G.cell_offset + (c2 * G.nc[1] + c1) * G.nc[0] + c0;
+  if (cell >= a.cells_cap) {  // unreachable: cells per structure <= 2n + 8
+    raise_error(a.status, TNEP_ERR_INVALID, s);
+    a.atom_cell[g] = -1;
+    return;
+  }
+  a.atom_cell[g] = cell;
+  a.atom_slot[g] = atomicAdd(&a.cell_count[cell], 1);
+}
+
+__global__ void k_scan_cells(NbrArgs a) {
+  const int n_cells = min(a.struct_cells[a.n_structs], a.cells_cap);
+  block_exclusive_scan(a.cell_count, a.cell_start, n_cells);
+}
+
+__global__ void k_scatter(NbrArgs a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_atoms) return;
+  const int cell = a.atom_cell[g];
+  if (cell < 0 || cell >= a.cells_cap) return;
+  a.cell_atoms[a.cell_start[cell] + a.atom_slot[g]] = g;
+}
+
+// One warp per cell: order by input index, write sorted arrays.
+__global__ void k_cell_sort(NbrArgs a, int* sorted_cell) {
+  const int n_cells = min(a.struct_cells[a.n_structs], a.cells_cap);
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_cells; c += warps) {
+  const int start = a.cell_start[c], m = a.cell_start[c + 1] - start;
+  for (int e = lane; e < m; e += 32) {
+    const int id = a.cell_atoms[start + e];
+    int rank = 0;
+    for (int f = 0; f < m; ++f) rank += (a.cell_atoms[start + f] < id);
+    const int dst = start + rank;
+    a.sorted_orig[dst] = id;
+    a.orig_sorted[id] = dst;
+    a.sorted_struct[dst] = a.atom_struct[id];
+    sorted_cell[dst] = c;
+    const int t = a.types[id % a.types_period];
+    a.pos4[dst] = make_float4(a.pos[3 * (size_t)id], a.pos[3 * (size_t)id + 1], a.pos[3 * (size_t)id + 2],
+                              __int_as_float(t));
+  }
+  }
+}
+
+__device__ __forceinline__ int axis_cells(int c, int nc, bool periodic, int k, int* out) {
+  int n = 0;
+  if (periodic) {
+    if (nc >= 2 * k + 1) {
+      for (int o = -k; o <= k; ++o) out[n++] = (c + o + nc) % nc;
+    } else {
+      for (int o = 0; o < nc; ++o) out[n++] = o;
+    }
+  } else {
+    const int lo = max(0, c - k), hi = min(nc - 1, c + k);
+    for (int o = lo; o <= hi; ++o) out[n++] = o;
+  }
+  return n;
+}
+
+// Minimum-image difference with every operation rounded separately.
+__device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
+  float d = __fsub_rn(xj, xi);
+  if (L > 0.0f) d = __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, invL))));
+  return d;
+}
+
+__global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell, float rc2R, float rc2A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_atoms) return;
+  const float4 pi = a.pos4[i];
+  const int s = a.sorted_struct[i];
+  const StructGrid G = a.grids[s];
+  const int lc = sorted_cell[i] - G.cell_offset;
+  const int cx = lc % G.nc[0], cy = (lc / G.nc[0]) % G.nc[1], cz = lc / (G.nc[0] * G.nc[1]);
+  int lx[5], ly[5], lz[5];
+  const int k = a.cell_div;
+  const int nx = axis_cells(cx, G.nc[0], G.L[0] > 0.0f, k, lx);
+  const int ny = axis_cells(cy, G.nc[1], G.L[1] > 0.0f, k, ly);
+  const int nz = axis_cells(cz, G.nc[2], G.L[2] > 0.0f, k, lz);
+  int cR = 0, cA = 0;
+  for (int iz = 0; iz < nz; ++iz) {
+    for (int iy = 0; iy < ny; ++iy) {
+      const int row = G.cell_offset + (lz[iz] * G.nc[1] + ly[iy]) * G.nc[0];
+      for (int ix = 0; ix < nx; ++ix) {
+        const int gc = row + lx[ix];
+        const int j0 = a.cell_start[gc], j1 = a.cell_start[gc + 1];
+        for (int j = j0; j < j1; ++j) {
+          const float4 pj = a.pos4[j];
+          const float dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
+          const float dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
+          const float dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
+          const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+          if (r2 < rc2R && j != i) {
+            if (cR < a.cap_R) a.nbr_R[nbr_index(i, cR, a.cap_R)] = j;
+            ++cR;
+            if (r2 < rc2A) {
+              if (cA < a.cap_A) a.nbr_A[nbr_index(i, cA, a.cap_A)] = j;
+              ++cA;
+            }
+          }
+        }
+      }
+    }
+  }
+  a.cnt_R[i] = cR;
+  a.cnt_A[i] = cA;
+  if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
+  if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
+}
+
+__global__ void k_export(int n, const int* sorted_orig, const int* nbr_R, const int* cnt_R, int cap_R,
+                         const int* nbr_A, const int* cnt_A, int cap_A, int* out_cnt_R, int* out_cnt_A,
+                         int* out_R, int out_cap_R, int* out_A, int out_cap_A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = sorted_orig[i];
+  const int nR = cnt_R[i], nA = cnt_A[i];
+  out_cnt_R[o] = nR;
+  out_cnt_A[o] = nA;
+  for (int k = 0; k < min(nR, min(cap_R, out_cap_R)); ++k)
+    out_R[(size_t)o * out_cap_R + k] = sorted_orig[nbr_R[nbr_index(i, k, cap_R)]];
+  for (int k = 0; k < min(nA, min(cap_A, out_cap_A)); ++k)
+    out_A[(size_t)o * out_cap_A + k] = sorted_orig[nbr_A[nbr_index(i, k, cap_A)]];
+}
+
+}  // namespace
+
+cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st) {
+  const int S = a.n_structs, N = a.n_atoms;
+  if (S <= 0) return cudaSuccess;
+  count_launches(N > 0 ? 7 : 3);
+  k_plan<<<S, 256, 0, st>>>(a);
+  k_scan_structs<<<1, 1024, 0, st>>>(a);
+  // The number of cells in use is known only on the device; the cell scan
+  // and the per-cell sort read it from struct_cells[S].
+  if (N > 0) k_bin<<<(N + 255) / 256, 256, 0, st>>>(a);
+  k_scan_cells<<<1, 1024, 0, st>>>(a);
+  if (N > 0) {
+    k_scatter<<<(N + 255) / 256, 256, 0, st>>>(a);
+    // sorted_cell reuses atom_slot (dead after the scatter)
+    k_cell_sort<<<1216, 256, 0, st>>>(a, a.atom_slot);
+    const float rc2R = a.rc_R * a.rc_R, rc2A = a.rc_A * a.rc_A;
+    k_build<<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_neighbors(int n_atoms, const int* sorted_orig, const int* orig_sorted,
+                                    const int* nbr_R, const int* cnt_R, int cap_R,
+                                    const int* nbr_A, const int* cnt_A, int cap_A,
+                                    int* out_cnt_R, int* out_cnt_A, int* out_R, int out_cap_R,
+                                    int* out_A, int out_cap_A, cudaStream_t st) {
+  (void)orig_sorted;
+  if (n_atoms <= 0) return cudaSuccess;
+  count_launches(1);
+  k_export<<<(n_atoms + 127) / 128, 128, 0, st>>>(n_atoms, sorted_orig, nbr_R, cnt_R, cap_R, nbr_A, cnt_A,
+                                                   cap_A, out_cnt_R, out_cnt_A, out_R, out_cap_R, out_A,
+                                                   out_cap_A);
+  return cudaGetLastError();
+}
+
+}  // namespace tnep

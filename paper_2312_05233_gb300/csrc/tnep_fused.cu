@@ -1,0 +1,614 @@
+// Fused TNEP kernel: descriptor -> network -> partial forces -> tensor contraction.
+//
+// One thread owns one atom i and walks its neighbour lists four times:
+//   1. radial forward   q_n   = sum_j g^R_n(r_ij)
+//   2. angular forward  A_nlm = sum_j g^A_n(r_ij) p_lm(u_ij)   (120 register accumulators)
+//      then q_nl = sum_m w_lm A_nlm^2 and the 4-body invariant
+//   3. network U_i = w1 . tanh(W0 s - b0) - b1 and dU/dq (Eq. 1)
+//   4. angular backward: partial force
+//        dU_i/dr_ij = s1 u + (V - (u.V) u) / r,
+//        s1 = sum_lm T_lm p_lm,  V = sum_lm S_lm grad p_lm,
+//        S_lm = sum_n G_nlm g_n(r),  T_lm = sum_n G_nlm g_n'(r),  G = dU/dA
+//   5. radial backward: dU_i/dr_ij = (sum_k D^{t_j}_k f_k'(r)) u,
+//        D^t_k = sum_n (dU/dq_n) c^{t_i t}_{nk}
+// and contracts each partial force on the fly (Sec. II.B-C):
+//   rank 1 (Eq. 3):  mu_i    -= |r_ij|^2 dU_i/dr_ij
+//   rank 2 (Eq. 4):  alpha_i -= r_ij (x) dU_i/dr_ij,  plus U_i on the diagonal.
+// Nothing per pair is stored: basis values are recomputed in the backward
+// walks.  Per-atom results go out in float32 (SoA) and are summed per
+// structure in float64 by the reduce kernel.
+//
+// Angular functions: real Cartesian polynomials p_lm(u) of the unit vector u
+// with weights w_lm such that P_l(a.b) = sum_m w_lm p_lm(a) p_lm(b) (the
+// addition theorem in a real, unnormalised basis).  With this basis
+// q_nl = sum_{j,k} g g P_l(cos theta_ijk) = sum_m w_lm A_nlm^2 exactly.
+// The l = 2 four-body invariant sum_m (2 2 2; m1 m2 m3) A A A equals
+// C4 * Tr(M^3), where M is the traceless symmetric tensor
+// sum_j g_n(r_ij) (u u^T - I/3) built from the five l = 2 sums, and
+// C4 = (2 2 2; 0 0 0) (5 / 4 pi)^(3/2) / (2/9) (evaluate both sides at
+// a = b = c = z_hat; the invariant is unique up to scale).
+
+#include <atomic>
+
+#include "tnep_internal.cuh"
+
+namespace tnep {
+
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+// (2 2 2; 0 0 0) = -sqrt(2/35);  C4 = -sqrt(2/35) * (5/(4 pi))^1.5 * 9/2
+constexpr float kC4 = -0.26998130975990770f;
+
+// Addition-theorem weights of the real polynomials, l = 1..4 (see real_harmonics):
+// w = (4 pi / (2l+1)) * (normalisation of the orthonormal real harmonic)^2.
+constexpr float wlm(int k) {
+  constexpr float w[24] = {1.f, 1.f, 1.f, 3.f, 3.f, 3.f, 0.75f, 0.25f, 0.625f, 15.f, 0.375f, 0.25f,
+                           0.375f, 3.75f, 0.625f, 8.75f, 4.375f, 1.25f, 0.625f, 0.015625f, 0.625f,
+                           0.3125f, 4.375f, 0.546875f};
+  return w[k];
+}
+constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : (k < 15 ? 3 : 4)); }
+
+// Real polynomials p_lm(x, y, z) on the unit sphere:
+// l=1: x, y, z
+// l=2: xy, yz, xz, x^2-y^2, 3z^2-1
+// l=3: y(3x^2-y^2), xyz, y(5z^2-1), z(5z^2-3), x(5z^2-1), z(x^2-y^2), x(x^2-3y^2)
+// l=4: xy(x^2-y^2), yz(3x^2-y^2), xy(7z^2-1), yz(7z^2-3), 35z^4-30z^2+3,
+//      xz(7z^2-3), (x^2-y^2)(7z^2-1), xz(x^2-3y^2), x^4-6x^2y^2+y^4
+template <int LMAX>
+__device__ __forceinline__ void real_harmonics(float x, float y, float z, float* p) {
+  p[0] = x; p[1] = y; p[2] = z;
+  if constexpr (LMAX >= 2) {
+    const float x2 = x * x, y2 = y * y, z2 = z * z;
+    p[3] = x * y; p[4] = y * z; p[5] = x * z; p[6] = x2 - y2; p[7] = 3.f * z2 - 1.f;
+    if constexpr (LMAX >= 3) {
+      const float t5 = 5.f * z2;
+      p[8] = y * (3.f * x2 - y2);
+      p[9] = x * y * z;
+      p[10] = y * (t5 - 1.f);
+      p[11] = z * (t5 - 3.f);
+      p[12] = x * (t5 - 1.f);
+      p[13] = z * (x2 - y2);
+      p[14] = x * (x2 - 3.f * y2);
+      if constexpr (LMAX >= 4) {
+        const float t7 = 7.f * z2;
+        p[15] = x * y * (x2 - y2);
+        p[16] = y * z * (3.f * x2 - y2);
+        p[17] = x * y * (t7 - 1.f);
+        p[18] = y * z * (t7 - 3.f);
+        p[19] = (35.f * z2 - 30.f) * z2 + 3.f;
+        p[20] = x * z * (t7 - 3.f);
+        p[21] = (x2 - y2) * (t7 - 1.f);
+        p[22] = x * z * (x2 - 3.f * y2);
+        p[23] = x2 * (x2 - 3.f * y2) - y2 * (3.f * x2 - y2);
+      }
+    }
+  }
+}
+
+// V += sum_lm S_lm * grad p_lm(x, y, z)  (gradient of the polynomial as written).
+template <int LMAX>
+__device__ __forceinline__ void harmonic_grad(const float* S, float x, float y, float z, float& vx, float& vy,
+                                              float& vz) {
+  vx += S[0]; vy += S[1]; vz += S[2];
+  if constexpr (LMAX >= 2) {
+    vx += y * S[3] + z * S[5] + 2.f * x * S[6];
+    vy += x * S[3] + z * S[4] - 2.f * y * S[6];
+    vz += y * S[4] + x * S[5] + 6.f * z * S[7];
+    if constexpr (LMAX >= 3) {
+      const float x2 = x * x, y2 = y * y, z2 = z * z;
+      const float xy = x * y, yz = y * z, xz = x * z;
+      const float t5 = 5.f * z2 - 1.f;
+      // p8 = 3x^2y - y^3
+      vx += 6.f * xy * S[8];
+      vy += (3.f * x2 - 3.f * y2) * S[8];
+      // p9 = xyz
+      vx += yz * S[9]; vy += xz * S[9]; vz += xy * S[9];
+      // p10 = y(5z^2-1)
+      vy += t5 * S[10]; vz += 10.f * yz * S[10];
+      // p11 = 5z^3 - 3z
+      vz += (15.f * z2 - 3.f) * S[11];
+      // p12 = x(5z^2-1)
+      vx += t5 * S[12]; vz += 10.f * xz * S[12];
+      // p13 = z(x^2-y^2)
+      vx += 2.f * xz * S[13]; vy -= 2.f * yz * S[13]; vz += (x2 - y2) * S[13];
+      // p14 = x^3 - 3xy^2
+      vx += (3.f * x2 - 3.f * y2) * S[14]; vy -= 6.f * xy * S[14];
+      if constexpr (LMAX >= 4) {
+        const float t7 = 7.f * z2 - 1.f;
+        const float xyz = xy * z;
+        // p15 = x^3 y - x y^3
+        vx += (3.f * x2 * y - y2 * y) * S[15];
+        vy += (x2 * x - 3.f * x * y2) * S[15];
+        // p16 = 3x^2yz - y^3 z
+        vx += 6.f * xyz * S[16];
+        vy += (3.f * x2 - 3.f * y2) * z * S[16];
+        vz += (3.f * x2 * y - y2 * y) * S[16];
+        // p17 = xy(7z^2-1)
+        vx += y * t7 * S[17]; vy += x * t7 * S[17]; vz += 14.f * xyz * S[17];
+        // p18 = 7yz^3 - 3yz
+        vy += (7.f * z2 - 3.f) * z * S[18];
+        vz += (21.f * z2 - 3.f) * y * S[18];
+        // p19 = 35z^4 - 30z^2 + 3
+        vz += (140.f * z2 - 60.f) * z * S[19];
+        // p20 = xz(7z^2-3)
+        vx += (7.f * z2 - 3.f) * z * S[20];
+        vz += (21.f * z2 - 3.f) * x * S[20];
+        // p21 = (x^2-y^2)(7z^2-1)
+        vx += 2.f * x * t7 * S[21]; vy -= 2.f * y * t7 * S[21]; vz += 14.f * z * (x2 - y2) * S[21];
+        // p22 = x^3 z - 3 x y^2 z
+        vx += (3.f * x2 - 3.f * y2) * z * S[22];
+        vy -= 6.f * xyz * S[22];
+        vz += (x2 * x - 3.f * x * y2) * S[22];
+        // p23 = x^4 - 6x^2y^2 + y^4
+        vx += (4.f * x2 * x - 12.f * x * y2) * S[23];
+        vy += (4.f * y2 * y - 12.f * x2 * y) * S[23];
+      }
+    }
+  }
+}
+
+// Chebyshev basis f_k = (T_k(x) + 1) f_c / 2, x = 2 (r/rc - 1)^2 - 1.
+template <int B>
+__device__ __forceinline__ void basis_fwd(float r, float rcinv, float* f) {
+  float sn, cs;
+  __sincosf(kPi * r * rcinv, &sn, &cs);
+  const float fc = 0.5f + 0.5f * cs;
+  const float t = r * rcinv - 1.f;
+  const float x = 2.f * t * t - 1.f;
+  const float hfc = 0.5f * fc;
+  f[0] = fc;
+  float T0 = 1.f, T1 = x;
+  if constexpr (B > 1) f[1] = hfc * (x + 1.f);
+#pragma unroll
+  for (int k = 2; k < B; ++k) {
+    const float T2 = 2.f * x * T1 - T0;
+    f[k] = hfc * (T2 + 1.f);
+    T0 = T1; T1 = T2;
+  }
+}
+
+// Basis and its radial derivative.
+template <int B>
+__device__ __forceinline__ void basis_fwd_bwd(float r, float rcinv, float* f, float* df) {
+  float sn, cs;
+  __sincosf(kPi * r * rcinv, &sn, &cs);
+  const float fc = 0.5f + 0.5f * cs;
+  const float dfc = -0.5f * kPi * rcinv * sn;
+  const float t = r * rcinv - 1.f;
+  const float x = 2.f * t * t - 1.f;
+  const float dx = 4.f * t * rcinv;
+  const float hfc = 0.5f * fc, hdfc = 0.5f * dfc, hdxfc = 0.5f * dx * fc;
+  f[0] = fc; df[0] = dfc;
+  float T0 = 1.f, T1 = x, dT0 = 0.f, dT1 = 1.f;
+  if constexpr (B > 1) { f[1] = hfc * (x + 1.f); df[1] = hdxfc + hdfc * (x + 1.f); }
+#pragma unroll
+  for (int k = 2; k < B; ++k) {
+    const float T2 = 2.f * x * T1 - T0;
+    const float dT2 = 2.f * T1 + 2.f * x * dT1 - dT0;
+    f[k] = hfc * (T2 + 1.f);
+    df[k] = hdxfc * dT2 + hdfc * (T2 + 1.f);
+    T0 = T1; T1 = T2; dT0 = dT1; dT1 = dT2;
+  }
+}
+
+// Loads one (t_i, t_j) coefficient block c[n][k] from shared memory.
+template <int NN, int B>
+__device__ __forceinline__ void load_coeffs(const float* blk, float* cc) {
+  constexpr int NV = (NN * B + 3) / 4;
+  const float4* c4 = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float4 t = c4[v];
+    cc[4 * v] = t.x; cc[4 * v + 1] = t.y; cc[4 * v + 2] = t.z; cc[4 * v + 3] = t.w;
+  }
+}
+
+__device__ __forceinline__ float min_image(float d, float L, float invL) {
+  return L > 0.f ? d - L * rintf(d * invL) : d;
+}
+
+// Tr(M^3) of the traceless symmetric M built from the l=2 sums a[0..4]
+// (xy, yz, xz, x^2-y^2, 3z^2-1), and its gradient with respect to a.
+__device__ __forceinline__ float trace_m3(const float* a, float* grad) {
+  const float mxy = a[0], myz = a[1], mxz = a[2];
+  const float mzz = a[4] * (1.f / 3.f);
+  const float mxx = 0.5f * (a[3] - mzz), myy = 0.5f * (-a[3] - mzz);
+  const float nxx = mxx * mxx + mxy * mxy + mxz * mxz;
+  const float nyy = mxy * mxy + myy * myy + myz * myz;
+  const float nzz = mxz * mxz + myz * myz + mzz * mzz;
+  const float nxy = mxx * mxy + mxy * myy + mxz * myz;
+  const float nyz = mxy * mxz + myy * myz + myz * mzz;
+  const float nxz = mxx * mxz + mxy * myz + mxz * mzz;
+  // Tr(M^3) = sum_ij M_ij (M^2)_ji
+  const float tr = mxx * nxx + myy * nyy + mzz * nzz + 2.f * (mxy * nxy + myz * nyz + mxz * nxz);
+  // d Tr(M^3) = 3 Tr(M^2 dM)
+  grad[0] = 6.f * nxy;
+  grad[1] = 6.f * nyz;
+  grad[2] = 6.f * nxz;
+  grad[3] = 1.5f * (nxx - nyy);
+  grad[4] = nzz - 0.5f * (nxx + nyy);
+  return tr;
+}
+
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK>
+__global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant__ FusedArgs a) {
+  constexpr int NLM = LMAX * (LMAX + 2);
+  constexpr int D = NR + NA * LMAX + (FB ? NA : 0);
+  constexpr int DP = (D + 3) & ~3;
+  constexpr int C = RANK == 1 ? 3 : 9;
+  constexpr int NBR4 = ((NR * BR + 3) / 4) * 4;
+  constexpr int NBA4 = ((NA * BA + 3) / 4) * 4;
+  extern __shared__ float4 sm4[];
+  float* sm = reinterpret_cast<float*>(sm4);
+  const ModelLayout& Ly = a.lay;
+  const int pop = blockIdx.y;
+  {
+    const float4* src = reinterpret_cast<const float4*>(a.model + (size_t)pop * a.model_stride);
+    for (int k = threadIdx.x; k < (Ly.words >> 2); k += blockDim.x) sm4[k] = src[k];
+  }
+  __syncthreads();
+  const int tid = threadIdx.x;
+  float* scratch = sm + Ly.words + tid;  // slot s at scratch[s * kFusedBlock]
+  const int i = blockIdx.x * kFusedBlock + tid;
+  if (i >= a.n_atoms) return;
+
+  const float4 pi = a.pos4[i];
+  const int ti = __float_as_int(pi.w);
+  const StructBox bx = a.boxes[a.sorted_struct[i]];
+  const int T = Ly.n_types;
+  const float rcRinv = 1.f / a.rc_R, rcAinv = 1.f / a.rc_A;
+
+  // ---------------------------------------------------------------- radial forward
+  float q[DP];
+#pragma unroll
+  for (int d = 0; d < DP; ++d) q[d] = 0.f;
+  const int nR = min(a.cnt_R[i], a.cap_R);
+  const float* cR_i = sm + Ly.off_cR + ti * T * Ly.stride_cR;
+  for (int kk = 0; kk < nR; ++kk) {
+    const int j = a.nbr_R[nbr_index(i, kk, a.cap_R)];
+    const float4 pj = a.pos4[j];
+    const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
+    const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
+    const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float r = r2 * rsqrtf(r2);
+    float f[BR];
+    basis_fwd<BR>(r, rcRinv, f);
+    float cc[NBR4];
+    load_coeffs<NR, BR>(cR_i + __float_as_int(pj.w) * Ly.stride_cR, cc);
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+      float g = 0.f;
+#pragma unroll
+      for (int k = 0; k < BR; ++k) g += cc[n * BR + k] * f[k];
+      q[n] += g;
+    }
+  }
+
+  // ---------------------------------------------------------------- angular forward
+  const int nA = min(a.cnt_A[i], a.cap_A);
+  const float* cA_i = sm + Ly.off_cA + ti * T * Ly.stride_cA;
+  {
+    float A[NA * NLM];
+#pragma unroll
+    for (int k = 0; k < NA * NLM; ++k) A[k] = 0.f;
+    for (int kk = 0; kk < nA; ++kk) {
+      const int j = a.nbr_A[nbr_index(i, kk, a.cap_A)];
+      const float4 pj = a.pos4[j];
+      const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
+      const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
+      const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv;
+      float f[BA];
+      basis_fwd<BA>(r, rcAinv, f);
+      float cc[NBA4];
+      load_coeffs<NA, BA>(cA_i + __float_as_int(pj.w) * Ly.stride_cA, cc);
+      float g[NA];
+#pragma unroll
+      for (int n = 0; n < NA; ++n) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < BA; ++k) s += cc[n * BA + k] * f[k];
+        g[n] = s;
+      }
+      float p[NLM];
+      real_harmonics<LMAX>(dx * rinv, dy * rinv, dz * rinv, p);
+#pragma unroll
+      for (int n = 0; n < NA; ++n)
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) A[n * NLM + lm] += g[n] * p[lm];
+    }
+    // descriptor components and stash of A for the backward pass
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        const float v = A[n * NLM + lm];
+        q[NR + (l_of(lm) - 1) * NA + n] += wlm(lm) * v * v;
+        scratch[(n * NLM + lm) * kFusedBlock] = v;
+      }
+      if constexpr (FB) {
+        float gr[5];
+        q[NR + LMAX * NA + n] = kC4 * trace_m3(&A[n * NLM + 3], gr);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- network (Eq. 1)
+  const int net = Ly.nets > 1 ? ti : 0;
+  const float* W0 = sm + Ly.off_W0 + net * Ly.H * DP;
+  const float* b0 = sm + Ly.off_b0 + net * Ly.H;
+  const float* w1 = sm + Ly.off_w1 + net * Ly.H;
+  const float* sc = sm + Ly.off_scaler;
+  float e[DP];
+  float U = -sm[Ly.off_b1 + net];
+  {
+    float s[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) { s[d] = q[d] * sc[d]; e[d] = 0.f; }
+    for (int h = 0; h < Ly.H; ++h) {
+      const float4* row = reinterpret_cast<const float4*>(W0 + h * DP);
+      float z = -b0[h];
+#pragma unroll
+      for (int v = 0; v < DP / 4; ++v) {
+        const float4 w = row[v];
+        z += w.x * s[4 * v] + w.y * s[4 * v + 1] + w.z * s[4 * v + 2] + w.w * s[4 * v + 3];
+      }
+      const float hh = tanhf(z);
+      const float wh = w1[h];
+      U += wh * hh;
+      const float vh = wh * (1.f - hh * hh);
+#pragma unroll
+      for (int v = 0; v < DP / 4; ++v) {
+        const float4 w = row[v];
+        e[4 * v] += vh * w.x; e[4 * v + 1] += vh * w.y; e[4 * v + 2] += vh * w.z; e[4 * v + 3] += vh * w.w;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < DP; ++d) e[d] *= sc[d];
+  }
+
+  float acc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] = 0.f;
+
+  // ---------------------------------------------------------------- angular backward
+  {
+    float G[NA * NLM];
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm)
+        G[n * NLM + lm] = 2.f * wlm(lm) * e[NR + (l_of(lm) - 1) * NA + n] * scratch[(n * NLM + lm) * kFusedBlock];
+      if constexpr (FB) {
+        float a2[5], gr[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) a2[m] = scratch[(n * NLM + 3 + m) * kFusedBlock];
+        trace_m3(a2, gr);
+        const float e4 = kC4 * e[NR + LMAX * NA + n];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) G[n * NLM + 3 + m] += e4 * gr[m];
+      }
+    }
+    for (int kk = 0; kk < nA; ++kk) {
+      const int j = a.nbr_A[nbr_index(i, kk, a.cap_A)];
+      const float4 pj = a.pos4[j];
+      const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
+      const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
+      const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv;
+      const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv;
+      float f[BA], df[BA];
+      basis_fwd_bwd<BA>(r, rcAinv, f, df);
+      float cc[NBA4];
+      load_coeffs<NA, BA>(cA_i + __float_as_int(pj.w) * Ly.stride_cA, cc);
+      float g[NA], dg[NA];
+#pragma unroll
+      for (int n = 0; n < NA; ++n) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < BA; ++k) { s0 += cc[n * BA + k] * f[k]; s1 += cc[n * BA + k] * df[k]; }
+        g[n] = s0; dg[n] = s1;
+      }
+      float p[NLM];
+      real_harmonics<LMAX>(ux, uy, uz, p);
+      float S[NLM];
+      float srad = 0.f;
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        float sv = 0.f, tv = 0.f;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) { sv += G[n * NLM + lm] * g[n]; tv += G[n * NLM + lm] * dg[n]; }
+        S[lm] = sv;
+        srad += tv * p[lm];
+      }
+      float vx = 0.f, vy = 0.f, vz = 0.f;
+      harmonic_grad<LMAX>(S, ux, uy, uz, vx, vy, vz);
+      const float uv = ux * vx + uy * vy + uz * vz;
+      const float fx = srad * ux + rinv * (vx - uv * ux);
+      const float fy = srad * uy + rinv * (vy - uv * uy);
+      const float fz = srad * uz + rinv * (vz - uv * uz);
+      if constexpr (RANK == 1) {
+        acc[0] -= r2 * fx; acc[1] -= r2 * fy; acc[2] -= r2 * fz;
+      } else {
+        acc[0] -= dx * fx; acc[1] -= dx * fy; acc[2] -= dx * fz;
+        acc[3] -= dy * fx; acc[4] -= dy * fy; acc[5] -= dy * fz;
+        acc[6] -= dz * fx; acc[7] -= dz * fy; acc[8] -= dz * fz;
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- radial backward
+  for (int t = 0; t < T; ++t) {
+    float cc[NBR4];
+    load_coeffs<NR, BR>(cR_i + t * Ly.stride_cR, cc);
+#pragma unroll
+    for (int k = 0; k < BR; ++k) {
+      float v = 0.f;
+#pragma unroll
+      for (int n = 0; n < NR; ++n) v += e[n] * cc[n * BR + k];
+      scratch[(t * BR + k) * kFusedBlock] = v;
+    }
+  }
+  for (int kk = 0; kk < nR; ++kk) {
+    const int j = a.nbr_R[nbr_index(i, kk, a.cap_R)];
+    const float4 pj = a.pos4[j];
+    const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
+    const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
+    const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    float f[BR], df[BR];
+    basis_fwd_bwd<BR>(r, rcRinv, f, df);
+    const float* Dt = scratch + __float_as_int(pj.w) * BR * kFusedBlock;
+    float gs = 0.f;
+#pragma unroll
+    for (int k = 0; k < BR; ++k) gs += Dt[k * kFusedBlock] * df[k];
+    const float fs = gs * rinv;  // dU/dr_ij = gs * u = gs * d / r
+    if constexpr (RANK == 1) {
+      const float w = -r2 * fs;
+      acc[0] += w * dx; acc[1] += w * dy; acc[2] += w * dz;
+    } else {
+      acc[0] -= dx * dx * fs; acc[1] -= dx * dy * fs; acc[2] -= dx * dz * fs;
+      acc[3] -= dy * dx * fs; acc[4] -= dy * dy * fs; acc[5] -= dy * dz * fs;
+      acc[6] -= dz * dx * fs; acc[7] -= dz * dy * fs; acc[8] -= dz * dz * fs;
+    }
+  }
+
+  // ---------------------------------------------------------------- per-atom output
+  float* out = a.per_atom + (size_t)pop * a.per_atom_stride;
+  if constexpr (RANK == 2) { acc[0] += U; acc[4] += U; acc[8] += U; }
+#pragma unroll
+  for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
+}
+
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB>
+cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
+  const dim3 grid((a.n_atoms + kFusedBlock - 1) / kFusedBlock, n_pop);
+  if (rank == 1) {
+    auto fn = k_fused<NR, NA, BR, BA, LMAX, FB, 1>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, kFusedBlock, smem, st>>>(a);
+  } else {
+    auto fn = k_fused<NR, NA, BR, BA, LMAX, FB, 2>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, kFusedBlock, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Per-structure FP64 sums (fixed order: strided per-thread sums, then a tree).
+__global__ void __launch_bounds__(256) k_reduce(const int* offsets, const float* per_atom, size_t pa_pop_stride,
+                                                int atom_stride, int C, double* out, size_t out_pop_stride) {
+  const int s = blockIdx.x, p = blockIdx.y;
+  const int a0 = offsets[s], a1 = offsets[s + 1];
+  const float* pa = per_atom + (size_t)p * pa_pop_stride;
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x)
+    for (int c = 0; c < C; ++c) acc[c] += (double)pa[(size_t)c * atom_stride + g];
+  __shared__ double red[9][256];
+  for (int c = 0; c < C; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < C; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < C) out[(size_t)p * out_pop_stride + (size_t)s * C + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_gather(int n, const int* orig_sorted, const float* pa, int atom_stride, int C, float* out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int i = orig_sorted[g];
+  for (int c = 0; c < C; ++c) out[(size_t)g * C + c] = pa[(size_t)c * atom_stride + i];
+}
+
+__global__ void k_rmse(int S, int C, const double* pred, const double* target, double* rmse) {
+  const int p = blockIdx.x;
+  const double* pp = pred + (size_t)p * S * C;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < S * C; k += blockDim.x) {
+    const double d = pp[k] - target[k];
+    acc += d * d;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rmse[p] = S * C > 0 ? sqrt(red[0] / (double)(S * C)) : 0.0;
+}
+
+}  // namespace
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb) {
+  if (nR == 5 && nA == 5 && bR == 9 && bA == 9 && lmax == 4 && fb) return kVarStd;
+  if (nR == 4 && nA == 3 && bR == 7 && bA == 6 && lmax == 3 && fb) return kVarSmall;
+  return -1;
+}
+
+size_t fused_smem_bytes(int variant, const ModelLayout& lay) {
+  int slots = 0;
+  if (variant == kVarStd) slots = 5 * 24;
+  if (variant == kVarSmall) slots = 3 * 15;
+  const int bR = variant == kVarStd ? 9 : 7;
+  slots = slots > lay.n_types * bR ? slots : lay.n_types * bR;
+  return (size_t)(lay.words + slots * kFusedBlock) * sizeof(float);
+}
+
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, cudaStream_t st) {
+  if (a.n_atoms <= 0 || n_pop <= 0) return cudaSuccess;
+  count_launches(1);
+  const size_t smem = fused_smem_bytes(variant, a.lay);
+  switch (variant) {
+    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, smem, st);
+    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, const float* per_atom,
+                          size_t per_atom_stride, int atom_stride, int C, double* out,
+                          size_t out_pop_stride, cudaStream_t st) {
+  if (n_structs <= 0 || n_pop <= 0) return cudaSuccess;
+  count_launches(1);
+  k_reduce<<<dim3(n_structs, n_pop), 256, 0, st>>>(offsets, per_atom, per_atom_stride, atom_stride, C, out,
+                                                  out_pop_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_per_atom(int n_atoms, const int* orig_sorted, const float* per_atom,
+                                   int atom_stride, int C, float* out, cudaStream_t st) {
+  if (n_atoms <= 0) return cudaSuccess;
+  count_launches(1);
+  k_gather<<<(n_atoms + 255) / 256, 256, 0, st>>>(n_atoms, orig_sorted, per_atom, atom_stride, C, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rmse(int n_pop, int n_structs, int C, const double* pred, const double* target,
+                        double* rmse, cudaStream_t st) {
+  if (n_pop <= 0) return cudaSuccess;
+  count_launches(1);
+  k_rmse<<<n_pop, 256, 0, st>>>(n_structs, C, pred, target, rmse);
+  return cudaGetLastError();
+}
+
+}  // namespace tnep

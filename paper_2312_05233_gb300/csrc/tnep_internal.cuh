@@ -1,0 +1,141 @@
+// Internal declarations shared by the CUDA translation units of libtnep.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tnep.h"
+
+namespace tnep {
+
+constexpr int kMaxTypes = 8;
+constexpr int kFusedBlock = 128;  // atoms per CTA of the fused kernel (one atom per thread)
+
+// Device-side status word, reset before each batch and read back after it.
+struct DevStatus {
+  int error;        // first tnep_status raised on the device (0 = none)
+  int bad_struct;   // structure that raised it
+  int max_cnt_R;    // largest radial neighbour count seen above the cap
+  int max_cnt_A;    // largest angular neighbour count seen above the cap
+};
+
+// Per-structure cell grid (orthorhombic, periodic or open per axis).
+struct StructGrid {
+  float L[3];       // periodic edge (0 = open axis)
+  float invL[3];    // 1/L rounded to float32 (0 on open axes)
+  float origin[3];  // grid origin (0 on periodic axes, min corner on open axes)
+  float cinv[3];    // cells per Angstrom
+  int nc[3];        // cells per axis
+  int cell_offset;  // first global cell of this structure
+};
+
+// Per-structure box as the fused kernel needs it.
+struct StructBox {
+  float L[3];
+  float invL[3];
+};
+
+// Neighbour lists are stored warp-tiled: entry k of atom i lives at
+// ((i >> 5) * cap + k) * 32 + (i & 31), so one warp's lists are contiguous
+// and every row of 32 entries is one 128-byte line.
+__host__ __device__ __forceinline__ size_t nbr_index(int i, int k, int cap) {
+  return ((size_t)(i >> 5) * cap + k) * 32 + (i & 31);
+}
+
+// Arguments of the neighbour-list pipeline.
+struct NbrArgs {
+  int n_structs;
+  int n_atoms;
+  const int* offsets;       // [S+1] device
+  const float* pos;         // [N][3] input order, device
+  const float* box;         // [S][3] device or null
+  const int* types;         // input types, device
+  int types_period;         // type of atom g = types[g % types_period]
+  float rc_R, rc_A;
+  int cell_div;             // cells have edge >= rc_R / cell_div
+  // outputs / scratch
+  StructGrid* grids;        // [S]
+  StructBox* boxes;         // [S]
+  int* struct_cells;        // [S+1] cells per structure, then exclusive scan
+  int* atom_struct;         // [N] structure of each input atom
+  int* atom_cell;           // [N]
+  int* atom_slot;           // [N]
+  int* cell_count;          // [cells_cap]
+  int* cell_start;          // [cells_cap + 1]
+  int* cell_atoms;          // [N] scatter target
+  int* sorted_orig;         // [N] sorted -> input index
+  int* orig_sorted;         // [N] input -> sorted index
+  int* sorted_struct;       // [N]
+  float4* pos4;             // [N] sorted positions, w = type bits
+  int* nbr_R; int* nbr_A;   // warp-tiled lists (sorted indices)
+  int* cnt_R; int* cnt_A;   // [N] true counts (may exceed caps)
+  int cap_R, cap_A;
+  int cells_cap;
+  DevStatus* status;
+};
+
+// Process-wide count of kernels this library has launched.
+void count_launches(int n);
+long long launches_total();
+
+// Launches the cell-list + neighbour pipeline on `st`.
+cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st);
+
+// Packed model layout in device memory (floats).
+struct ModelLayout {
+  int n_types, nets, H, D, Dp;
+  int stride_cR, stride_cA;        // floats per (ti, tj) coefficient block
+  int off_cR, off_cA, off_W0, off_b0, off_w1, off_b1, off_scaler;
+  int words;                       // total floats, multiple of 4
+};
+
+// Arguments of the fused descriptor -> network -> partial force -> contraction kernel.
+struct FusedArgs {
+  int n_atoms;
+  const float4* pos4;
+  const int* sorted_struct;
+  const StructBox* boxes;
+  const int* nbr_R; const int* cnt_R; int cap_R;
+  const int* nbr_A; const int* cnt_A; int cap_A;
+  const float* model;        // packed model (first individual)
+  size_t model_stride;       // floats between individuals (population), 0 otherwise
+  ModelLayout lay;
+  float rc_R, rc_A;
+  float* per_atom;           // [pop][C][atom_stride] (SoA, sorted order)
+  size_t per_atom_stride;    // floats between individuals
+  int atom_stride;           // row stride of the SoA output
+};
+
+// Kernel variant keys (must match the compiled instantiations).
+enum Variant { kVarStd = 0, kVarSmall = 1, kVarCount = 2 };
+
+int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb);
+size_t fused_smem_bytes(int variant, const ModelLayout& lay);
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, cudaStream_t st);
+
+// Per-structure FP64 reduction of per-atom contributions.
+cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, const float* per_atom,
+                          size_t per_atom_stride, int atom_stride, int C, double* out,
+                          size_t out_pop_stride, cudaStream_t st);
+
+// Gathers per-atom contributions back to input order: out[g][c] = pa[c][orig_sorted[g]].
+cudaError_t launch_gather_per_atom(int n_atoms, const int* orig_sorted, const float* per_atom,
+                                   int atom_stride, int C, float* out, cudaStream_t st);
+
+// Converts warp-tiled sorted-index lists to row-major input-order lists.
+cudaError_t launch_export_neighbors(int n_atoms, const int* sorted_orig, const int* orig_sorted,
+                                    const int* nbr_R, const int* cnt_R, int cap_R,
+                                    const int* nbr_A, const int* cnt_A, int cap_A,
+                                    int* out_cnt_R, int* out_cnt_A, int* out_R, int out_cap_R,
+                                    int* out_A, int out_cap_A, cudaStream_t st);
+
+// RMSE per individual: rmse[p] = sqrt(mean_{s,c} (pred[p][s][c] - target[s][c])^2).
+cudaError_t launch_rmse(int n_pop, int n_structs, int C, const double* pred, const double* target,
+                        double* rmse, cudaStream_t st);
+
+// Spectrum tail.
+cudaError_t launch_spectrum(const double* series, int T, int C, double dt_fs, int kind, int M,
+                            int subtract_mean, double* work /* >= T*9 + 2*(M+1) + 2*M doubles */,
+                            double* freq, double* spec, double* acf_out, cudaStream_t st);
+
+}  // namespace tnep

@@ -1,0 +1,341 @@
+"""Python binding of libtnep (ctypes): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it converts numpy arrays or torch tensors into
+pointers and sizes, calls the library and raises TnepError on a non-zero
+status.  All computation runs in the CUDA kernels of libtnep.so; there is no
+CPU fallback, and importing this module fails loudly if the library has not
+been built.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtnep.so")
+
+TNEP_OK = 0
+STATUS_NAMES = {
+    0: "TNEP_OK", 1: "TNEP_ERR_INVALID", 2: "TNEP_ERR_OOM", 3: "TNEP_ERR_BOX_TOO_SMALL",
+    4: "TNEP_ERR_NEIGHBOR_OVERFLOW", 5: "TNEP_ERR_CUDA", 6: "TNEP_ERR_TIMEOUT",
+    7: "TNEP_ERR_UNSUPPORTED", 8: "TNEP_ERR_BUSY", 9: "TNEP_ERR_NO_DEVICE",
+}
+TNEP_SPECTRUM_IR, TNEP_SPECTRUM_RAMAN_ISO, TNEP_SPECTRUM_RAMAN_ANISO = 0, 1, 2
+(TNEP_OPT_FRAMES_PER_BATCH, TNEP_OPT_MAX_NEIGHBORS, TNEP_OPT_BLOCK_ATOMS, TNEP_OPT_LAST_KERNEL_MS,
+ TNEP_OPT_CELL_DIV, TNEP_OPT_LAST_KERNEL_LAUNCHES, TNEP_OPT_LAST_NBR_MS,
+ TNEP_OPT_KERNEL_LAUNCHES_TOTAL) = range(8)
+
+# Every symbol include/tnep.h declares (tests check the library exports them).
+EXPORTED = [
+    "tnep_create", "tnep_destroy", "tnep_last_error", "tnep_output_dim", "tnep_eval",
+    "tnep_eval_batch", "tnep_neighbors", "tnep_eval_population", "tnep_spectrum",
+    "tnep_set_option", "tnep_get_option",
+]
+
+
+class TnepError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [
+        ("rank", C.c_int), ("n_max_R", C.c_int), ("n_max_A", C.c_int), ("basis_R", C.c_int),
+        ("basis_A", C.c_int), ("l_max", C.c_int), ("use_4body", C.c_int), ("n_hidden", C.c_int),
+        ("per_type_nn", C.c_int), ("params", C.POINTER(C.c_float)), ("n_params", C.c_size_t),
+        ("q_scaler", C.POINTER(C.c_float)), ("mlp_precision", C.c_int),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2312_05233_gb300.build.build() first")
+    lib = C.CDLL(LIB_PATH)
+    vp, ip, fp, dp = C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_void_p
+    sig = {
+        "tnep_create": (C.c_int, [C.POINTER(ModelDesc), C.c_int, C.c_int, C.POINTER(C.c_char_p),
+                                  C.POINTER(C.c_float), C.c_int, C.POINTER(vp)]),
+        "tnep_destroy": (None, [vp]),
+        "tnep_last_error": (C.c_char_p, []),
+        "tnep_output_dim": (C.c_int, [vp, C.c_int]),
+        "tnep_eval": (C.c_int, [vp, C.c_int, C.c_int, fp, fp, vp, dp, vp]),
+        "tnep_eval_batch": (C.c_int, [vp, C.c_int, ip, fp, fp, vp, dp, fp, vp]),
+        "tnep_neighbors": (C.c_int, [vp, C.c_int, ip, fp, fp, vp, vp, vp, C.c_int, vp, C.c_int, vp]),
+        "tnep_eval_population": (C.c_int, [vp, C.c_int, C.c_int, fp, C.c_int, ip, fp, fp, vp, dp, dp, dp, vp]),
+        "tnep_spectrum": (C.c_int, [dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, vp]),
+        "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
+        "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(status: int):
+    if status != TNEP_OK:
+        raise TnepError(status, _lib.tnep_last_error().decode(errors="replace"))
+
+
+# ------------------------------------------------------------------ marshalling
+class _Buf:
+    """A contiguous buffer and its pointer; keeps host copies alive."""
+
+    def __init__(self, x, dtype, name, writable=False):
+        self.obj = None
+        self.ptr = None
+        if x is None:
+            return
+        try:
+            import torch
+            if isinstance(x, torch.Tensor):
+                tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+                if x.dtype != tdt or not x.is_contiguous():
+                    if writable:
+                        raise TypeError(f"{name} must be a contiguous {tdt} tensor")
+                    x = x.to(tdt).contiguous()
+                self.obj = x
+                self.ptr = x.data_ptr()
+                return
+        except ImportError:
+            pass
+        a = np.asarray(x)
+        if writable:
+            if a.dtype != dtype or not a.flags.c_contiguous or not a.flags.writeable:
+                raise TypeError(f"{name} must be a writable C-contiguous {np.dtype(dtype).name} array")
+        else:
+            a = np.ascontiguousarray(a, dtype=dtype)
+        self.obj = a
+        self.ptr = a.ctypes.data if a.size else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+@dataclass
+class Model:
+    """A model for tnep_create: hyper-parameters plus flat float32 parameters."""
+
+    rank: int
+    params: np.ndarray
+    n_max_R: int = 4
+    n_max_A: int = 4
+    basis_R: int = 8
+    basis_A: int = 8
+    l_max: int = 4
+    use_4body: int = 1
+    n_hidden: int = 30
+    per_type_nn: int = 1
+    q_scaler: np.ndarray | None = None
+    mlp_precision: int = 0
+
+    @classmethod
+    def from_hyper(cls, hp, params, q_scaler=None, mlp_precision=0):
+        return cls(rank=hp.rank, params=params, n_max_R=hp.n_max_R, n_max_A=hp.n_max_A,
+                   basis_R=hp.basis_R, basis_A=hp.basis_A, l_max=hp.l_max, use_4body=hp.use_4body,
+                   n_hidden=hp.n_hidden, per_type_nn=hp.per_type_nn, q_scaler=q_scaler,
+                   mlp_precision=mlp_precision)
+
+
+class Context:
+    """Owns a tnep_ctx handle; the methods are the C entry points."""
+
+    def __init__(self, handle, models, n_types):
+        self.handle = handle
+        self.models = models
+        self.n_types = n_types
+        self.dims = [_lib.tnep_output_dim(handle, k) for k in range(len(models))]
+
+    def close(self):
+        if self.handle:
+            _lib.tnep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def tnep_create(models, n_types: int, cutoffs=(6.0, 4.0), device: int = 0, type_names=None) -> Context:
+    models = list(models)
+    descs = (ModelDesc * len(models))()
+    keep = []
+    for k, m in enumerate(models):
+        p = np.ascontiguousarray(m.params, dtype=np.float32)
+        s = None if m.q_scaler is None else np.ascontiguousarray(m.q_scaler, dtype=np.float32)
+        keep += [p, s]
+        d = descs[k]
+        d.rank, d.n_max_R, d.n_max_A = m.rank, m.n_max_R, m.n_max_A
+        d.basis_R, d.basis_A, d.l_max, d.use_4body = m.basis_R, m.basis_A, m.l_max, m.use_4body
+        d.n_hidden, d.per_type_nn, d.mlp_precision = m.n_hidden, m.per_type_nn, m.mlp_precision
+        d.params = p.ctypes.data_as(C.POINTER(C.c_float))
+        d.n_params = p.size
+        d.q_scaler = s.ctypes.data_as(C.POINTER(C.c_float)) if s is not None else None
+    cut = (C.c_float * 2)(float(cutoffs[0]), float(cutoffs[1]))
+    names = None
+    if type_names is not None:
+        names = (C.c_char_p * len(type_names))(*[n.encode() for n in type_names])
+    h = C.c_void_p()
+    _check(_lib.tnep_create(descs, len(models), int(n_types), names, cut, int(device), C.byref(h)))
+    return Context(h, models, n_types)
+
+
+def tnep_set_option(ctx: Context, option: int, value: float):
+    _check(_lib.tnep_set_option(ctx.handle, int(option), float(value)))
+
+
+def tnep_get_option(ctx: Context, option: int) -> float:
+    v = C.c_double()
+    _check(_lib.tnep_get_option(ctx.handle, int(option), C.byref(v)))
+    return v.value
+
+
+def _alloc_out(like_device, shape, dtype):
+    if like_device is not None:
+        import torch
+        return torch.empty(shape, dtype={np.float64: torch.float64, np.float32: torch.float32}[dtype],
+                           device=like_device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _device_of(x):
+    try:
+        import torch
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            return x.device
+    except ImportError:
+        pass
+    return None
+
+
+def tnep_eval(ctx: Context, pos, box, types, out=None, stream=None):
+    """pos [F][N][3], box [F][3] or [3] or None, types [N] -> out [n_models][F][C] blocks.
+
+    Returns a list with one [F][C_m] array (or tensor) per model."""
+    shp = tuple(pos.shape)
+    F, N = int(shp[0]), int(shp[1])
+    if box is not None and np.ndim(np.asarray(box.cpu() if hasattr(box, "cpu") else box)) == 1:
+        b = np.asarray(box.cpu() if hasattr(box, "cpu") else box, dtype=np.float32)
+        box = np.ascontiguousarray(np.broadcast_to(b, (F, 3)))
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    T = _Buf(types, np.int32, "types")
+    tot = sum(ctx.dims)
+    if out is None:
+        out = _alloc_out(_device_of(pos), (F * tot,), np.float64)
+    O = _Buf(out, np.float64, "out", writable=True)
+    _check(_lib.tnep_eval(ctx.handle, F, N, P.ptr, B.ptr, T.ptr, O.ptr, _stream_ptr(stream)))
+    res, off = [], 0
+    for c in ctx.dims:
+        res.append(out[off:off + F * c].reshape(F, c))
+        off += F * c
+    return res
+
+
+def tnep_eval_batch(ctx: Context, offsets, pos, box, types, per_atom=False, out=None, stream=None):
+    """Uneven structures: offsets [S+1] (host), pos [N][3], box [S][3] or None, types [N].
+
+    Returns (list of [S][C_m], list of [N][C_m] per-atom arrays or None)."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    N = int(offs[-1])
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    T = _Buf(types, np.int32, "types")
+    tot = sum(ctx.dims)
+    dev = _device_of(pos)
+    if out is None:
+        out = _alloc_out(dev, (S * tot,), np.float64)
+    O = _Buf(out, np.float64, "out", writable=True)
+    pa = _alloc_out(dev, (N * tot,), np.float32) if per_atom else None
+    PA = _Buf(pa, np.float32, "per_atom", writable=True)
+    _check(_lib.tnep_eval_batch(ctx.handle, S, offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr, T.ptr,
+                                O.ptr, PA.ptr if per_atom else None, _stream_ptr(stream)))
+    res, pres, off, poff = [], [], 0, 0
+    for c in ctx.dims:
+        res.append(out[off:off + S * c].reshape(S, c))
+        off += S * c
+        if per_atom:
+            pres.append(pa[poff:poff + N * c].reshape(N, c))
+            poff += N * c
+    return res, (pres if per_atom else None)
+
+
+def tnep_neighbors(ctx: Context, offsets, pos, box, cap_R=256, cap_A=128, stream=None):
+    """Returns (counts_R [N], counts_A [N], list_R [N][cap_R], list_A [N][cap_A]) as numpy."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    N = int(offs[-1])
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    cR = np.zeros(N, np.int32)
+    cA = np.zeros(N, np.int32)
+    lR = np.full((N, cap_R), -1, np.int32)
+    lA = np.full((N, cap_A), -1, np.int32)
+    _check(_lib.tnep_neighbors(ctx.handle, S, offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr,
+                               cR.ctypes.data, cA.ctypes.data, lR.ctypes.data, cap_R, lA.ctypes.data, cap_A,
+                               _stream_ptr(stream)))
+    return cR, cA, lR, lA
+
+
+def tnep_eval_population(ctx: Context, model: int, params, offsets, pos, box, types, target,
+                         want_out=False, stream=None):
+    """params [P][n_params] (host) -> (rmse [P], predictions [P][S][C] or None)."""
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    Pn = prm.shape[0]
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    c = ctx.dims[model]
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    T = _Buf(types, np.int32, "types")
+    TG = _Buf(target, np.float64, "target")
+    rmse = np.zeros(Pn, np.float64)
+    out = np.zeros((Pn, S, c), np.float64) if want_out else None
+    _check(_lib.tnep_eval_population(ctx.handle, int(model), Pn, prm.ctypes.data, S,
+                                     offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr, T.ptr, TG.ptr,
+                                     rmse.ctypes.data, out.ctypes.data if want_out else None,
+                                     _stream_ptr(stream)))
+    return rmse, out
+
+
+def tnep_spectrum(series, dt_fs: float, kind: int = TNEP_SPECTRUM_IR, max_lag: int = 0, subtract_mean=True,
+                  want_acf=False, stream=None):
+    """series [T][3 or 9] float64 (host or device) -> (freq_cm1, spec[, acf]) numpy."""
+    S = _Buf(series, np.float64, "series")
+    Tn, Cn = int(series.shape[0]), int(series.shape[1])
+    M = Tn // 2 if max_lag <= 0 else int(max_lag)
+    freq = np.zeros(M + 1)
+    spec = np.zeros(M + 1)
+    acf = np.zeros(M + 1) if want_acf else None
+    _check(_lib.tnep_spectrum(S.ptr, Tn, Cn, float(dt_fs), int(kind), int(max_lag), int(bool(subtract_mean)),
+                              freq.ctypes.data, spec.ctypes.data, acf.ctypes.data if want_acf else None,
+                              _stream_ptr(stream)))
+    return (freq, spec, acf) if want_acf else (freq, spec)

@@ -1,0 +1,94 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects bad arguments with the documented status codes
+before it touches a device."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2312_05233_gb300 import tnep
+    return tnep
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "tnep.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tnep_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_library_exports(tn):
+    syms = header_symbols()
+    assert len(syms) >= 11
+    lib = tn.lib()
+    for s in syms:
+        assert hasattr(lib, s), f"libtnep.so does not export {s}"
+    assert sorted(tn.EXPORTED) == sorted(syms)
+
+
+def _desc(tn, **over):
+    import synth
+    hp = synth.HyperParams(n_types=2, rank=1)
+    p = synth.model_params(hp, np.random.default_rng(0))
+    m = tn.Model.from_hyper(hp, p)
+    for k, v in over.items():
+        setattr(m, k, v)
+    return m
+
+
+def _create_status(tn, models, n_types=2, cut=(6.0, 4.0)):
+    try:
+        ctx = tn.tnep_create(models, n_types, cut)
+    except tn.TnepError as e:
+        return e.status
+    ctx.close()
+    return 0
+
+
+def test_create_validation(tn):
+    assert _create_status(tn, []) == 1
+    assert _create_status(tn, [_desc(tn)], n_types=0) == 1
+    assert _create_status(tn, [_desc(tn)], n_types=9) == 1
+    assert _create_status(tn, [_desc(tn)], cut=(4.0, 6.0)) == 1
+    assert _create_status(tn, [_desc(tn, rank=3)]) == 1
+    assert _create_status(tn, [_desc(tn, n_hidden=65)]) == 1
+    bad = _desc(tn)
+    bad.params = bad.params[:-1]
+    assert _create_status(tn, [bad]) == 1
+    assert _create_status(tn, [_desc(tn, l_max=6)]) in (1, 7)
+    assert _create_status(tn, [_desc(tn, mlp_precision=2)]) == 1
+
+
+def test_create_without_gpu_reports_no_device(tn):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert _create_status(tn, [_desc(tn)]) == 9
+
+
+def test_null_context_and_spectrum_validation(tn):
+    lib = tn.lib()
+    assert lib.tnep_eval(None, 1, 1, None, None, None, None, None) == 1
+    assert lib.tnep_set_option(None, 0, 1.0) == 1
+    v = C.c_double()
+    assert lib.tnep_get_option(None, 0, C.byref(v)) == 1
+    assert lib.tnep_output_dim(None, 0) == 0
+    s = np.zeros((10, 3))
+    f = np.zeros(6)
+    sp = np.zeros(6)
+    # C must match the kind, T >= 2, dt > 0, 1 <= max_lag < T
+    assert lib.tnep_spectrum(s.ctypes.data, 10, 9, 1.0, 0, 5, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
+    assert lib.tnep_spectrum(s.ctypes.data, 1, 3, 1.0, 0, 5, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
+    assert lib.tnep_spectrum(s.ctypes.data, 10, 3, 0.0, 0, 5, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
+    assert lib.tnep_spectrum(s.ctypes.data, 10, 3, 1.0, 0, 10, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
+    assert lib.tnep_spectrum(s.ctypes.data, 10, 3, 1.0, 7, 5, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
+    assert "kind" in lib.tnep_last_error().decode()

@@ -1,0 +1,327 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances.  The CUDA path computes in float32 (descriptors, network,
+partial forces, per-atom contractions) and sums atoms per structure in
+float64.  The bar is a per-frame relative error of 1e-5 in the Frobenius
+norm (float32 rounding of ~1e2 neighbour terms per atom gives ~1e-6; the
+margin covers the hardware sine/cosine in the cutoff, ~4e-7 absolute).  When
+a tensor is a cancelling sum, its norm is compared against the condition
+scale sum_i |per-atom contribution_i| instead (an error of 1e-6 of it).
+Neighbour lists are compared as exact sets.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+RC = (6.0, 4.0)
+REL = 1e-5
+COND = 1e-6
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2312_05233_gb300 import tnep
+    return tnep
+
+
+def models_for(tn, n_types, ranks=(1, 2), seed=11, small=False, per_type_nn=1, scaler=True):
+    rng = np.random.default_rng(seed)
+    out, orc = [], []
+    for r in ranks:
+        if small:
+            hp = synth.HyperParams(n_types=n_types, rank=r, n_max_R=3, n_max_A=2, basis_R=6, basis_A=5,
+                                   l_max=3, use_4body=1, n_hidden=17, per_type_nn=per_type_nn)
+        else:
+            hp = synth.HyperParams(n_types=n_types, rank=r, per_type_nn=per_type_nn)
+        p = synth.model_params(hp, rng)
+        sc = synth.default_q_scaler(hp) if scaler else None
+        out.append(tn.Model.from_hyper(hp, p, sc))
+        orc.append(oracle.OracleModel.from_flat(hp, p, sc, *RC))
+    return out, orc
+
+
+def check_frames(got, ref, per_atom_ref=None):
+    got = np.asarray(got)
+    for f in range(len(ref)):
+        err = np.linalg.norm(got[f] - ref[f])
+        scale = np.linalg.norm(ref[f])
+        tol = REL * scale
+        if per_atom_ref is not None:
+            tol = max(tol, COND * np.abs(per_atom_ref[f]).sum())
+        assert err <= tol, f"frame {f}: |d|={err:.3e} |ref|={scale:.3e} tol={tol:.3e}"
+
+
+# ----------------------------------------------------------- neighbour lists
+@pytest.mark.parametrize("cell_div", [1, 2])
+def test_neighbors_bitexact(tn, cell_div):
+    frames, types, box = synth.water_small(3)
+    structs = [synth.Structure(frames[f], types, box) for f in range(3)]
+    rng = np.random.default_rng(3)
+    for n in (1, 7, 40):
+        p, t, b = synth.water_cluster(n, rng)
+        structs.append(synth.Structure(p.astype(np.float32), t, b.astype(np.float32)))
+    bt = synth.concat_structures(structs)
+    ms, _ = models_for(tn, 2, ranks=(1,))
+    ctx = tn.tnep_create(ms, 2, RC)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_CELL_DIV, cell_div)
+    cR, cA, lR, lA = tn.tnep_neighbors(ctx, bt.offsets, bt.pos, bt.box, cap_R=256, cap_A=128)
+    for s in range(bt.n_structs):
+        a0, a1 = bt.offsets[s], bt.offsets[s + 1]
+        refR = oracle.neighbours_fp32(bt.pos[a0:a1], bt.box[s], RC[0])
+        refA = oracle.neighbours_fp32(bt.pos[a0:a1], bt.box[s], RC[1])
+        for a in range(a1 - a0):
+            g = a0 + a
+            assert cR[g] == len(refR[a]) and cA[g] == len(refA[a])
+            assert np.array_equal(np.sort(lR[g, :cR[g]]) - a0, refR[a])
+            assert np.array_equal(np.sort(lA[g, :cA[g]]) - a0, refA[a])
+    ctx.close()
+
+
+# ------------------------------------------------------- small water (192 atoms)
+def test_water_small_parity(tn):
+    frames, types, box = synth.water_small(12)
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    mu, alpha = tn.tnep_eval(ctx, frames, box, types)
+    for got, m in ((mu, om[0]), (alpha, om[1])):
+        res = [oracle.evaluate(m, frames[f], box, types) for f in range(len(frames))]
+        check_frames(got, np.array([r.tensor for r in res]), np.array([r.per_atom for r in res]))
+    ctx.close()
+
+
+def test_device_and_host_inputs_agree(tn):
+    frames, types, box = synth.water_small(5)
+    ms, _ = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    h = tn.tnep_eval(ctx, frames, box, types)
+    d = tn.tnep_eval(ctx, torch.from_numpy(frames).cuda(), torch.from_numpy(box).cuda(),
+                     torch.from_numpy(types).cuda())
+    for a, b in zip(h, d):
+        assert np.array_equal(a, b.cpu().numpy())
+    ctx.close()
+
+
+def test_batch_split_is_bitwise_invariant(tn):
+    """Results do not depend on how frames are grouped into device passes."""
+    frames, types, box = synth.water_small(9)
+    ms, _ = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    outs = []
+    for fb in (1, 4, 9):
+        tn.tnep_set_option(ctx, tn.TNEP_OPT_FRAMES_PER_BATCH, fb)
+        outs.append(tn.tnep_eval(ctx, frames, box, types))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+    ctx.close()
+
+
+def test_per_atom_parity(tn):
+    frames, types, box = synth.water_small(1)
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    offs = np.array([0, len(types)])
+    (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, offs, frames[0], box[None], types, per_atom=True)
+    for got, m, tot in ((pmu, om[0], mu), (pal, om[1], al)):
+        ref = oracle.evaluate(m, frames[0], box, types).per_atom
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(got, ref, atol=REL * scale, rtol=0)
+        # the structure total is the FP64 sum of the per-atom contributions
+        np.testing.assert_allclose(tot[0], got.astype(np.float64).sum(0), rtol=1e-12, atol=1e-12 * scale)
+    ctx.close()
+
+
+# ------------------------------------------- second kernel variant, 3 types
+@pytest.mark.parametrize("per_type_nn", [1, 0])
+def test_small_variant_three_types(tn, per_type_nn):
+    rng = np.random.default_rng(5)
+    base, types, box = synth.bzo_supercell(3)
+    frames = synth.thermal_frames(base, box, 3, 0.08, rng)
+    box = box.astype(np.float32)
+    ms, om = models_for(tn, 3, small=True, per_type_nn=per_type_nn)
+    ctx = tn.tnep_create(ms, 3, RC)
+    outs = tn.tnep_eval(ctx, frames, box, types)
+    for got, m in zip(outs, om):
+        res = [oracle.evaluate(m, frames[f], box, types) for f in range(len(frames))]
+        check_frames(got, np.array([r.tensor for r in res]), np.array([r.per_atom for r in res]))
+    ctx.close()
+
+
+# ------------------------------------------------- uneven batch, edge cases
+def test_uneven_batch_open_and_periodic(tn):
+    rng = np.random.default_rng(17)
+    structs = []
+    for n in (5, 1, 30):
+        p, t, b = synth.water_cluster(n, rng)
+        structs.append(synth.Structure(p.astype(np.float32), t, b.astype(np.float32)))
+    structs.append(synth.Structure(np.zeros((0, 3), np.float32), np.zeros(0, np.int32), np.zeros(3, np.float32)))
+    structs.append(synth.Structure(np.array([[1.0, 2.0, 3.0]], np.float32), np.array([1], np.int32),
+                                   np.zeros(3, np.float32)))
+    p, t, b = synth.water_box(64, rng, L=12.42)
+    structs.append(synth.Structure(np.mod(p, b).astype(np.float32), t, b.astype(np.float32)))
+    # one axis open, two periodic (a slab)
+    p, t, b = synth.water_box(64, rng, L=12.42)
+    structs.append(synth.Structure(p.astype(np.float32), t, np.array([12.42, 12.42, 0.0], np.float32)))
+    bt = synth.concat_structures(structs)
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    outs, _ = tn.tnep_eval_batch(ctx, bt.offsets, bt.pos, bt.box, bt.types)
+    for got, m in zip(outs, om):
+        res = []
+        for s in range(bt.n_structs):
+            a0, a1 = bt.offsets[s], bt.offsets[s + 1]
+            res.append(oracle.evaluate(m, bt.pos[a0:a1], bt.box[s], bt.types[a0:a1]))
+        ref = np.array([r.tensor for r in res])
+        pa = [np.abs(r.per_atom).sum() for r in res]
+        for s in range(bt.n_structs):
+            err = np.linalg.norm(got[s] - ref[s])
+            assert err <= max(REL * np.linalg.norm(ref[s]), COND * pa[s], 1e-12), (s, err, ref[s])
+    assert np.all(outs[0][3] == 0) and np.all(outs[1][3] == 0)  # empty structure
+    ctx.close()
+
+
+def test_six_type_anions(tn):
+    rng = np.random.default_rng(23)
+    structs = []
+    for n in (20, 37, 60):
+        p, t, b = synth.anion(n, rng)
+        structs.append(synth.Structure(p.astype(np.float32), t, b.astype(np.float32)))
+    bt = synth.concat_structures(structs)
+    ms, om = models_for(tn, 6)
+    ctx = tn.tnep_create(ms, 6, RC)
+    outs, _ = tn.tnep_eval_batch(ctx, bt.offsets, bt.pos, bt.box, bt.types)
+    for got, m in zip(outs, om):
+        for s in range(bt.n_structs):
+            a0, a1 = bt.offsets[s], bt.offsets[s + 1]
+            r = oracle.evaluate(m, bt.pos[a0:a1], bt.box[s], bt.types[a0:a1])
+            err = np.linalg.norm(got[s] - r.tensor)
+            assert err <= max(REL * np.linalg.norm(r.tensor), COND * np.abs(r.per_atom).sum())
+    ctx.close()
+
+
+def test_errors_and_neighbor_regrow(tn):
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    p = np.zeros((2, 3), np.float32)
+    p[1] = [1.0, 0, 0]
+    with pytest.raises(tn.TnepError) as e:
+        tn.tnep_eval_batch(ctx, [0, 2], p, np.array([[11.0, 20.0, 20.0]], np.float32), np.array([0, 1]))
+    assert e.value.status == 3
+    with pytest.raises(tn.TnepError) as e:
+        tn.tnep_eval_batch(ctx, [0, 2], p, None, np.array([0, 2]))
+    assert e.value.status == 1
+    # 100 molecules in a 12.42 A cube (1.56x water density): more radial
+    # neighbours than the initial list capacity of 128, so the lists regrow
+    rng = np.random.default_rng(2)
+    pos, types, box = synth.water_box(100, rng, L=12.42)
+    pos = np.mod(pos, box).astype(np.float32)
+    box = box.astype(np.float32)
+    cR, cA, _, _ = tn.tnep_neighbors(ctx, [0, len(types)], pos, box[None], cap_R=8, cap_A=8)
+    assert cR.max() > 128
+    (mu, al), _ = tn.tnep_eval_batch(ctx, [0, len(types)], pos, box[None], types)
+    for got, m in ((mu, om[0]), (al, om[1])):
+        r = oracle.evaluate(m, pos, box, types)
+        assert np.linalg.norm(got[0] - r.tensor) <= max(REL * np.linalg.norm(r.tensor),
+                                                        COND * np.abs(r.per_atom).sum())
+    if cR.max() > 32:
+        ctx2 = tn.tnep_create(ms, 2, RC)
+        tn.tnep_set_option(ctx2, tn.TNEP_OPT_MAX_NEIGHBORS, 32)
+        with pytest.raises(tn.TnepError) as e:
+            tn.tnep_eval_batch(ctx2, [0, len(types)], pos, box[None], types)
+        assert e.value.status == 4
+        ctx2.close()
+    ctx.close()
+
+
+# ------------------------------------------- full-size workloads, sampled atoms
+def test_bulk_water_full_size_sampled(tn):
+    frames, types, box = synth.water_bulk(n_frames=2)
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    N = len(types)
+    offs = np.array([0, N])
+    (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, offs, frames[1], box[None], types, per_atom=True)
+    sample = np.random.default_rng(0).choice(N, size=200, replace=False)
+    for got, m in ((pmu, om[0]), (pal, om[1])):
+        ref = oracle.evaluate(m, frames[1], box, types, centers=sample).per_atom[sample]
+        np.testing.assert_allclose(got[sample], ref, atol=REL * np.abs(ref).max(), rtol=0)
+    np.testing.assert_allclose(mu[0], pmu.astype(np.float64).sum(0), rtol=1e-12, atol=1e-9)
+    # the same frame through the trajectory path gives the same numbers
+    mu2, al2 = tn.tnep_eval(ctx, frames, box, types)
+    assert np.array_equal(mu2[1], mu[0]) and np.array_equal(al2[1], al[0])
+    ctx.close()
+
+
+def test_perovskite_full_size_symmetry_and_sample(tn):
+    base, types, box = synth.bzo_supercell(12)
+    base = base.astype(np.float32)
+    box = box.astype(np.float32)
+    ms, om = models_for(tn, 3, ranks=(1, 2))
+    ctx = tn.tnep_create(ms, 3, RC)
+    (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, [0, len(types)], base, box[None], types, per_atom=True)
+    cond = np.abs(pal).sum()
+    # perfect cubic lattice: mu = 0 and alpha = a I (Sec. II.C equivariance)
+    assert np.abs(mu[0]).max() <= COND * np.abs(pmu).sum()
+    a = al[0].reshape(3, 3)
+    assert np.abs(a - a[0, 0] * np.eye(3)).max() <= COND * cond
+    frames = synth.bzo_perovskite(n_frames=1)[0]
+    (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, [0, len(types)], frames[0], box[None], types, per_atom=True)
+    sample = np.random.default_rng(1).choice(len(types), size=150, replace=False)
+    for got, m in ((pmu, om[0]), (pal, om[1])):
+        ref = oracle.evaluate(m, frames[0], box, types, centers=sample).per_atom[sample]
+        np.testing.assert_allclose(got[sample], ref, atol=REL * np.abs(ref).max(), rtol=0)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- population
+def test_population_matches_individual_evaluation(tn):
+    rng = np.random.default_rng(31)
+    structs = synth.population_structures(n_clusters=6, n_boxes=3, seed_k=1)
+    bt = synth.concat_structures(structs)
+    hp = synth.HyperParams(n_types=2, rank=1)
+    P = 5
+    params = np.stack([synth.model_params(hp, rng) for _ in range(P)])
+    sc = synth.default_q_scaler(hp)
+    target = rng.standard_normal((bt.n_structs, 3))
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc)], 2, RC)
+    rmse, pred = tn.tnep_eval_population(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target,
+                                         want_out=True)
+    for p in range(P):
+        c1 = tn.tnep_create([tn.Model.from_hyper(hp, params[p], sc)], 2, RC)
+        (single,), _ = tn.tnep_eval_batch(c1, bt.offsets, bt.pos, bt.box, bt.types)
+        assert np.array_equal(single, pred[p])
+        c1.close()
+        assert rmse[p] == pytest.approx(np.sqrt(np.mean((pred[p] - target) ** 2)), rel=1e-12)
+    om = oracle.OracleModel.from_flat(hp, params[2], sc, *RC)
+    for s in (0, bt.n_structs - 1):
+        a0, a1 = bt.offsets[s], bt.offsets[s + 1]
+        r = oracle.evaluate(om, bt.pos[a0:a1], bt.box[s], bt.types[a0:a1])
+        assert np.linalg.norm(pred[2][s] - r.tensor) <= max(REL * np.linalg.norm(r.tensor),
+                                                            COND * np.abs(r.per_atom).sum())
+    ctx.close()
+
+
+# ------------------------------------------------------------------ spectra
+@pytest.mark.parametrize("kind,C", [(0, 3), (1, 9), (2, 9)])
+def test_spectrum_parity(tn, kind, C):
+    rng = np.random.default_rng(kind)
+    T = 600
+    t = np.arange(T)
+    series = rng.normal(size=(T, C)) + np.cos(0.07 * t)[:, None] * rng.normal(size=C)
+    f, S, acf = tn.tnep_spectrum(series, 0.5, kind, max_lag=250, want_acf=True)
+    fr, Sr = oracle.spectrum(series, 0.5, kind, max_lag=250)
+    Cr = oracle.acf(series, 250, kind)
+    np.testing.assert_allclose(acf, Cr, rtol=1e-11, atol=1e-13 * np.abs(Cr).max())
+    np.testing.assert_allclose(f, fr, rtol=1e-13)
+    np.testing.assert_allclose(S, Sr, rtol=1e-9, atol=1e-11 * np.abs(Sr).max())
+    # device-resident series gives the same result
+    f2, S2 = tn.tnep_spectrum(torch.from_numpy(series).cuda(), 0.5, kind, max_lag=250)
+    assert np.array_equal(S2, S)
