@@ -271,6 +271,7 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   a.box = d_box;
   a.types = d_types;
   a.types_period = std::max(types_period, 1);
+  a.n_types = c->n_types;
   a.rc_R = c->rc_R;
   a.rc_A = c->rc_A;
   a.cell_div = c->cell_div;

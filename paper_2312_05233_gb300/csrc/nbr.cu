@@ -205,7 +205,11 @@ __global__ void k_cell_sort(NbrArgs a, int* sorted_cell) {
     a.orig_sorted[id] = dst;
     a.sorted_struct[dst] = a.atom_struct[id];
     sorted_cell[dst] = c;
-    const int t = a.types[id % a.types_period];
+    int t = a.types[id % a.types_period];
+    if (t < 0 || t >= a.n_types) {
+      raise_error(a.status, TNEP_ERR_INVALID, a.atom_struct[id]);
+      t = 0;
+    }
     a.pos4[dst] = make_float4(a.pos[3 * (size_t)id], a.pos[3 * (size_t)id + 1], a.pos[3 * (size_t)id + 2],
                               __int_as_float(t));
   }

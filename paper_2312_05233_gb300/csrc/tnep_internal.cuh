@@ -51,6 +51,7 @@ struct NbrArgs {
   const float* box;         // [S][3] device or null
   const int* types;         // input types, device
   int types_period;         // type of atom g = types[g % types_period]
+  int n_types;              // types outside [0, n_types) raise TNEP_ERR_INVALID (and read as 0)
   float rc_R, rc_A;
   int cell_div;             // cells have edge >= rc_R / cell_div
   // outputs / scratch
