@@ -267,11 +267,20 @@ def test_perovskite_full_size_symmetry_and_sample(tn):
     ms, om = models_for(tn, 3, ranks=(1, 2))
     ctx = tn.tnep_create(ms, 3, RC)
     (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, [0, len(types)], base, box[None], types, per_atom=True)
-    cond = np.abs(pal).sum()
-    # perfect cubic lattice: mu = 0 and alpha = a I (Sec. II.C equivariance)
-    assert np.abs(mu[0]).max() <= COND * np.abs(pmu).sum()
+    # Every atom of the perfect lattice sits on an inversion centre, so its
+    # own contribution to mu vanishes and equivalent atoms carry identical
+    # float32 residuals that add coherently.  The yardstick is the pair-level
+    # scale sum_ij |r_ij|^k |dU_i/dr_ij| (k = 2 for mu, 1 for alpha),
+    # estimated from the oracle on a sample of centres.
+    sample = np.arange(0, len(types), 97)
+    scales = []
+    for m, k in ((om[0], 2), (om[1], 1)):
+        r = oracle.evaluate(m, base, box, types, centers=sample)
+        d = np.linalg.norm(r.rij, axis=1)
+        scales.append((d ** k * np.linalg.norm(r.dUdr, axis=1)).sum() * len(types) / len(sample))
+    assert np.abs(mu[0]).max() <= COND * scales[0]
     a = al[0].reshape(3, 3)
-    assert np.abs(a - a[0, 0] * np.eye(3)).max() <= COND * cond
+    assert np.abs(a - a[0, 0] * np.eye(3)).max() <= COND * scales[1]
     frames = synth.bzo_perovskite(n_frames=1)[0]
     (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, [0, len(types)], frames[0], box[None], types, per_atom=True)
     sample = np.random.default_rng(1).choice(len(types), size=150, replace=False)
