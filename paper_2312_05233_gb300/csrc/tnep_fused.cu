@@ -205,8 +205,19 @@ __device__ __forceinline__ void load_coeffs(const float* blk, float* cc) {
   }
 }
 
-__device__ __forceinline__ float min_image(float d, float L, float invL) {
-  return L > 0.f ? d - L * rintf(d * invL) : d;
+// Minimum-image component of r_ij = r_j - r_i.  The image shift k is taken
+// from the plain difference; the box edge is then subtracted from the operand
+// that lies near the far face before the final difference, which is exact
+// (Sterbenz) for positions wrapped into [0, L): pairs across a face keep the
+// precision of short vectors instead of rounding at ulp(L).
+__device__ __forceinline__ float min_image(float xj, float xi, float L, float invL) {
+  if (L > 0.f) {
+    const float k = rintf((xj - xi) * invL);
+    const float aj = fmaf(-fmaxf(k, 0.f), L, xj);
+    const float ai = fmaf(-fmaxf(-k, 0.f), L, xi);
+    return aj - ai;
+  }
+  return xj - xi;
 }
 
 // Tr(M^3) of the traceless symmetric M built from the l=2 sums a[0..4]
@@ -269,9 +280,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
   for (int kk = 0; kk < nR; ++kk) {
     const int j = a.nbr_R[nbr_index(i, kk, a.cap_R)];
     const float4 pj = a.pos4[j];
-    const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
-    const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
-    const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+    const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
+    const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
+    const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float r = r2 * rsqrtf(r2);
     float f[BR];
@@ -297,9 +308,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
     for (int kk = 0; kk < nA; ++kk) {
       const int j = a.nbr_A[nbr_index(i, kk, a.cap_A)];
       const float4 pj = a.pos4[j];
-      const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
-      const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
-      const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+      const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
+      const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
+      const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float rinv = rsqrtf(r2);
       const float r = r2 * rinv;
@@ -397,9 +408,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
     for (int kk = 0; kk < nA; ++kk) {
       const int j = a.nbr_A[nbr_index(i, kk, a.cap_A)];
       const float4 pj = a.pos4[j];
-      const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
-      const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
-      const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+      const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
+      const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
+      const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float rinv = rsqrtf(r2);
       const float r = r2 * rinv;
@@ -459,9 +470,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
   for (int kk = 0; kk < nR; ++kk) {
     const int j = a.nbr_R[nbr_index(i, kk, a.cap_R)];
     const float4 pj = a.pos4[j];
-    const float dx = min_image(pj.x - pi.x, bx.L[0], bx.invL[0]);
-    const float dy = min_image(pj.y - pi.y, bx.L[1], bx.invL[1]);
-    const float dz = min_image(pj.z - pi.z, bx.L[2], bx.invL[2]);
+    const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
+    const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
+    const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
