@@ -108,6 +108,8 @@ struct Workspace {
   DevBuf<StructBox> boxes;
   DevBuf<float> per_atom;   // [model][pop][C][atom_stride]
   DevBuf<double> out;       // [model][S][C]
+  DevBuf<double> partial;   // reduction partials
+  int max_atoms = 0;        // largest structure of the batch
   DevBuf<float> pos_stage[2], box_stage;
   DevBuf<int> types_stage;
   int atom_stride = 0;
@@ -118,7 +120,7 @@ struct Workspace {
                     &sorted_orig, &orig_sorted, &sorted_struct, &struct_cells, &cnt_R, &cnt_A, &nbr_R, &nbr_A,
                     &types_stage})
       b->release();
-    pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release();
+    pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release(); partial.release();
     pos_stage[0].release(); pos_stage[1].release(); box_stage.release();
   }
 };
@@ -239,6 +241,9 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   Workspace& w = c->ws;
   const int N = h_offsets[S];
   const int stride = round_up(std::max(N, 1), 32);
+  int mx = 0;
+  for (int s = 0; s < S; ++s) mx = std::max(mx, h_offsets[s + 1] - h_offsets[s]);
+  w.max_atoms = mx;
   w.atom_stride = stride;
   w.cells_cap = 2 * N + 8 * S;
   w.cap_R = c->cap_R;
@@ -369,11 +374,12 @@ tnep_status run_models(tnep_ctx* c, cudaStream_t st, int S, int N, cudaEvent_t e
     TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, st));
   }
   if (ev_done) TNEP_CUDA(cudaEventRecord(ev_done, st));
+  TNEP_CUDA(w.partial.ensure((size_t)std::max(S, 1) * reduce_chunks(w.max_atoms) * 9));
   size_t off = 0;
   for (size_t k = 0; k < c->models.size(); ++k) {
     const Model& m = c->models[k];
-    TNEP_CUDA(launch_reduce(S, 1, w.offsets.p, w.per_atom.p + k * per_model, 0, w.atom_stride, m.C,
-                            w.out.p + off, 0, st));
+    TNEP_CUDA(launch_reduce(S, 1, w.offsets.p, w.max_atoms, w.per_atom.p + k * per_model, 0, w.atom_stride, m.C,
+                            w.partial.p, w.out.p + off, 0, st));
     off += (size_t)S * m.C;
   }
   return TNEP_OK;
@@ -840,8 +846,9 @@ tnep_status tnep_eval_population(tnep_ctx* c, int model, int n_pop, const float*
     TNEP_CUDA(cudaEventRecord(ev[1], st));
     TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, n_pop, st));
     TNEP_CUDA(cudaEventRecord(ev[2], st));
-    TNEP_CUDA(launch_reduce(n_structs, n_pop, w.offsets.p, w.per_atom.p, pa_pop, w.atom_stride, m.C, w.out.p,
-                            (size_t)n_structs * m.C, st));
+    TNEP_CUDA(w.partial.ensure((size_t)n_pop * n_structs * reduce_chunks(w.max_atoms) * m.C));
+    TNEP_CUDA(launch_reduce(n_structs, n_pop, w.offsets.p, w.max_atoms, w.per_atom.p, pa_pop, w.atom_stride, m.C,
+                            w.partial.p, w.out.p, (size_t)n_structs * m.C, st));
     TNEP_CUDA(launch_rmse(n_pop, n_structs, m.C, w.out.p, d_target, c->pop_rmse.p, st));
     bool regrow = false;
     TNEP_TRY(finish(c, st, &regrow));

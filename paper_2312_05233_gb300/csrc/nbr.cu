@@ -33,12 +33,14 @@ __global__ void k_plan(NbrArgs a) {
   float L[3];
   for (int d = 0; d < 3; ++d) L[d] = a.box ? a.box[3 * s + d] : 0.0f;
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x) {
-    a.atom_struct[g] = s;
-    for (int d = 0; d < 3; ++d) {
-      const float x = a.pos[3 * (size_t)g + d];
-      mn[d] = fminf(mn[d], x);
-      mx[d] = fmaxf(mx[d], x);
+  const bool any_open = !(L[0] > 0.0f && L[1] > 0.0f && L[2] > 0.0f);
+  if (any_open) {  // bounding box of the open axes
+    for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x) {
+      for (int d = 0; d < 3; ++d) {
+        const float x = a.pos[3 * (size_t)g + d];
+        mn[d] = fminf(mn[d], x);
+        mx[d] = fmaxf(mx[d], x);
+      }
     }
   }
   __shared__ float smn[3][32], smx[3][32];
@@ -161,7 +163,14 @@ __device__ __forceinline__ int cell_coord(float x, const StructGrid& G, int d) {
 __global__ void k_bin(NbrArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n_atoms) return;
-  const int s = a.atom_struct[g];
+  // structure of atom g: last s with offsets[s] <= g
+  int lo = 0, hi = a.n_structs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.offsets[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const int s = lo;
+  a.atom_struct[g] = s;
   const StructGrid G = a.grids[s];
   const int c0 = cell_coord(a.pos[3 * (size_t)g + 0], G, 0);
   const int c1 = cell_coord(a.pos[3 * (size_t)g + 1], G, 1);

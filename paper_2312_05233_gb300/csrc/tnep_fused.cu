@@ -220,6 +220,30 @@ __device__ __forceinline__ float min_image(float xj, float xi, float L, float in
   return xj - xi;
 }
 
+// Software-pipelined walk over one atom's neighbour list: the neighbour index
+// is fetched two iterations ahead and its position one iteration ahead, so
+// the dependent index -> position gather overlaps the current pair's math.
+// Out-of-range slots re-use a valid index (loads stay in bounds).
+struct NbrWalk {
+  const int* __restrict__ list;
+  const float4* __restrict__ pos;
+  int i, cap, n;
+  int j_ahead;
+  float4 p_ahead;
+  __device__ __forceinline__ NbrWalk(const int* l, const float4* p, int i_, int cap_, int n_, float4 self)
+      : list(l), pos(p), i(i_), cap(cap_), n(n_) {
+    const int j0 = n > 0 ? list[nbr_index(i, 0, cap)] : i;
+    j_ahead = n > 1 ? list[nbr_index(i, 1, cap)] : j0;
+    p_ahead = n > 0 ? pos[j0] : self;
+  }
+  __device__ __forceinline__ float4 next(int k) {
+    const float4 pj = p_ahead;
+    p_ahead = pos[j_ahead];
+    if (k + 2 < n) j_ahead = list[nbr_index(i, k + 2, cap)];
+    return pj;
+  }
+};
+
 // Tr(M^3) of the traceless symmetric M built from the l=2 sums a[0..4]
 // (xy, yz, xz, x^2-y^2, 3z^2-1), and its gradient with respect to a.
 __device__ __forceinline__ float trace_m3(const float* a, float* grad) {
@@ -277,9 +301,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
   for (int d = 0; d < DP; ++d) q[d] = 0.f;
   const int nR = min(a.cnt_R[i], a.cap_R);
   const float* cR_i = sm + Ly.off_cR + ti * T * Ly.stride_cR;
+  NbrWalk wR(a.nbr_R, a.pos4, i, a.cap_R, nR, pi);
   for (int kk = 0; kk < nR; ++kk) {
-    const int j = a.nbr_R[nbr_index(i, kk, a.cap_R)];
-    const float4 pj = a.pos4[j];
+    const float4 pj = wR.next(kk);
     const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
     const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
     const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
@@ -305,9 +329,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
     float A[NA * NLM];
 #pragma unroll
     for (int k = 0; k < NA * NLM; ++k) A[k] = 0.f;
+    NbrWalk wA(a.nbr_A, a.pos4, i, a.cap_A, nA, pi);
     for (int kk = 0; kk < nA; ++kk) {
-      const int j = a.nbr_A[nbr_index(i, kk, a.cap_A)];
-      const float4 pj = a.pos4[j];
+      const float4 pj = wA.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
       const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
       const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
@@ -405,9 +429,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
         for (int m = 0; m < 5; ++m) G[n * NLM + 3 + m] += e4 * gr[m];
       }
     }
+    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, nA, pi);
     for (int kk = 0; kk < nA; ++kk) {
-      const int j = a.nbr_A[nbr_index(i, kk, a.cap_A)];
-      const float4 pj = a.pos4[j];
+      const float4 pj = wB.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
       const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
       const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
@@ -467,9 +491,9 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
       scratch[(t * BR + k) * kFusedBlock] = v;
     }
   }
+  NbrWalk wS(a.nbr_R, a.pos4, i, a.cap_R, nR, pi);
   for (int kk = 0; kk < nR; ++kk) {
-    const int j = a.nbr_R[nbr_index(i, kk, a.cap_R)];
-    const float4 pj = a.pos4[j];
+    const float4 pj = wS.next(kk);
     const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
     const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
     const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
@@ -517,26 +541,51 @@ cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, size_t smem,
   return cudaGetLastError();
 }
 
-// Per-structure FP64 sums (fixed order: strided per-thread sums, then a tree).
-__global__ void __launch_bounds__(256) k_reduce(const int* offsets, const float* per_atom, size_t pa_pop_stride,
-                                                int atom_stride, int C, double* out, size_t out_pop_stride) {
-  const int s = blockIdx.x, p = blockIdx.y;
-  const int a0 = offsets[s], a1 = offsets[s + 1];
+// Per-structure FP64 sums in two deterministic stages: CTA (s, chunk) sums a
+// fixed 2048-atom chunk of structure s (strided per-thread sums, then a
+// tree), then one thread per structure adds its chunk partials in order.
+// Chunks are aligned to the structure start, so a structure's result does
+// not depend on what else is in the batch.
+__global__ void __launch_bounds__(256) k_reduce_partial(const int* offsets, int n_chunks, const float* per_atom,
+                                                        size_t pa_pop_stride, int atom_stride, int C,
+                                                        double* partial) {
+  const int s = blockIdx.x / n_chunks, chunk = blockIdx.x % n_chunks, p = blockIdx.y;
+  const int S = gridDim.x / n_chunks;
+  const int a0 = offsets[s] + chunk * kReduceChunk;
+  const int a1 = min(offsets[s + 1], a0 + kReduceChunk);
   const float* pa = per_atom + (size_t)p * pa_pop_stride;
   double acc[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-  for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x)
-    for (int c = 0; c < C; ++c) acc[c] += (double)pa[(size_t)c * atom_stride + g];
+  for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      if (c < C) acc[c] += (double)pa[(size_t)c * atom_stride + g];
+  }
   __shared__ double red[9][256];
-  for (int c = 0; c < C; ++c) red[c][threadIdx.x] = acc[c];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) red[c][threadIdx.x] = acc[c];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w)
-      for (int c = 0; c < C; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < C) out[(size_t)p * out_pop_stride + (size_t)s * C + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < C) partial[(((size_t)p * S + s) * n_chunks + chunk) * C + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_reduce_final(int S, int n_chunks, int C, int n_pop, const double* partial, double* out,
+                               size_t out_pop_stride) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= S * n_pop) return;
+  const int p = t / S, s = t % S;
+  const double* src = partial + ((size_t)p * S + s) * n_chunks * C;
+  for (int c = 0; c < C; ++c) {
+    double v = 0.0;
+    for (int k = 0; k < n_chunks; ++k) v += src[(size_t)k * C + c];
+    out[(size_t)p * out_pop_stride + (size_t)s * C + c] = v;
+  }
 }
 
 __global__ void k_gather(int n, const int* orig_sorted, const float* pa, int atom_stride, int C, float* out) {
@@ -596,13 +645,16 @@ cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, c
   }
 }
 
-cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, const float* per_atom,
-                          size_t per_atom_stride, int atom_stride, int C, double* out,
+cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, int max_atoms, const float* per_atom,
+                          size_t per_atom_stride, int atom_stride, int C, double* partial, double* out,
                           size_t out_pop_stride, cudaStream_t st) {
   if (n_structs <= 0 || n_pop <= 0) return cudaSuccess;
-  count_launches(1);
-  k_reduce<<<dim3(n_structs, n_pop), 256, 0, st>>>(offsets, per_atom, per_atom_stride, atom_stride, C, out,
-                                                  out_pop_stride);
+  count_launches(2);
+  const int n_chunks = reduce_chunks(max_atoms);
+  k_reduce_partial<<<dim3(n_structs * n_chunks, n_pop), 256, 0, st>>>(offsets, n_chunks, per_atom, per_atom_stride,
+                                                                     atom_stride, C, partial);
+  const int nt = n_structs * n_pop;
+  k_reduce_final<<<(nt + 127) / 128, 128, 0, st>>>(n_structs, n_chunks, C, n_pop, partial, out, out_pop_stride);
   return cudaGetLastError();
 }
 

@@ -114,9 +114,12 @@ int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb);
 size_t fused_smem_bytes(int variant, const ModelLayout& lay);
 cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, cudaStream_t st);
 
-// Per-structure FP64 reduction of per-atom contributions.
-cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, const float* per_atom,
-                          size_t per_atom_stride, int atom_stride, int C, double* out,
+// Per-structure FP64 reduction of per-atom contributions.  `max_atoms` is
+// the largest structure; `partial` holds n_pop * n_structs * reduce_chunks(max_atoms) * C doubles.
+constexpr int kReduceChunk = 2048;
+inline int reduce_chunks(int max_atoms) { return max_atoms > 0 ? (max_atoms + kReduceChunk - 1) / kReduceChunk : 1; }
+cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, int max_atoms, const float* per_atom,
+                          size_t per_atom_stride, int atom_stride, int C, double* partial, double* out,
                           size_t out_pop_stride, cudaStream_t st);
 
 // Gathers per-atom contributions back to input order: out[g][c] = pa[c][orig_sorted[g]].
