@@ -184,6 +184,31 @@ tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int 
                           int max_lag, int subtract_mean, double* freq_cm1, double* spec,
                           double* acf_out, void* stream);
 
+/* Longest series tnep_spectrum_noalloc accepts (its scratch is sized for it). */
+#define TNEP_NOALLOC_MAX_T 32768
+
+/* The spectrum tail of tnep_spectrum without any device allocation.  The
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc, such as an MD engine that reserves all device memory for its
+ * own arena at start-up, or that computes spectra inside its time-step loop
+ * where cudaMalloc / cudaFree would add a device-wide synchronisation.
+ *   series [T][C] and the outputs freq_cm1 [M+1], spec [M+1], acf_out [M+1]
+ *   (or NULL) must be device memory; arguments and results are as in
+ *   tnep_spectrum.  T <= TNEP_NOALLOC_MAX_T, else TNEP_ERR_INVALID.
+ * Scratch lives in one file-scope device array of about 3 MB
+ * ((12 * TNEP_NOALLOC_MAX_T) doubles) that every GPU which loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * device's address of the array (once per device); make that first call
+ * before any stream capture.  The call is asynchronous on `stream`: results
+ * are ready once the stream has synchronised.  All calls share the one
+ * array, so calls that overlap on the GPU (different streams, or different
+ * host threads) race on it; order them on one stream.  Nothing from the
+ * previous call has to be cleared: every scratch element is written before
+ * it is read.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+tnep_status tnep_spectrum_noalloc(const double* series, int T, int C, double dt_fs, int kind,
+                                  int max_lag, int subtract_mean, double* freq_cm1, double* spec,
+                                  double* acf_out, void* stream);
+
 /* Tunables (tnep_set_option / tnep_get_option). */
 enum {
   TNEP_OPT_FRAMES_PER_BATCH = 0,    /* frames per device pass in tnep_eval (0 = automatic) */

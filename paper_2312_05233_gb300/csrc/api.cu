@@ -143,6 +143,8 @@ int coeff_stride(int words) {
 
 }  // namespace
 
+void tnep::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 struct tnep_ctx {
   int device = 0;
   cudaStream_t stream = nullptr, copy_stream = nullptr;

@@ -75,6 +75,9 @@ struct NbrArgs {
   DevStatus* status;
 };
 
+// Sets the thread-local message returned by tnep_last_error().
+void set_last_error(const char* msg);
+
 // Process-wide count of kernels this library has launched.
 void count_launches(int n);
 long long launches_total();

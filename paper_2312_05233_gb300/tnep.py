@@ -34,8 +34,9 @@ TNEP_SPECTRUM_IR, TNEP_SPECTRUM_RAMAN_ISO, TNEP_SPECTRUM_RAMAN_ANISO = 0, 1, 2
 EXPORTED = [
     "tnep_create", "tnep_destroy", "tnep_last_error", "tnep_output_dim", "tnep_eval",
     "tnep_eval_batch", "tnep_neighbors", "tnep_eval_population", "tnep_spectrum",
-    "tnep_set_option", "tnep_get_option",
+    "tnep_set_option", "tnep_get_option", "tnep_spectrum_noalloc",
 ]
+TNEP_NOALLOC_MAX_T = 32768
 
 
 class TnepError(RuntimeError):
@@ -69,6 +70,8 @@ def _load():
         "tnep_neighbors": (C.c_int, [vp, C.c_int, ip, fp, fp, vp, vp, vp, C.c_int, vp, C.c_int, vp]),
         "tnep_eval_population": (C.c_int, [vp, C.c_int, C.c_int, fp, C.c_int, ip, fp, fp, vp, dp, dp, dp, vp]),
         "tnep_spectrum": (C.c_int, [dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, vp]),
+        "tnep_spectrum_noalloc": (C.c_int, [dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp,
+                                            dp, vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -339,3 +342,17 @@ def tnep_spectrum(series, dt_fs: float, kind: int = TNEP_SPECTRUM_IR, max_lag: i
                               freq.ctypes.data, spec.ctypes.data, acf.ctypes.data if want_acf else None,
                               _stream_ptr(stream)))
     return (freq, spec, acf) if want_acf else (freq, spec)
+
+
+def tnep_spectrum_noalloc(series, dt_fs: float, kind: int, freq_out, spec_out, acf_out=None, max_lag: int = 0,
+                          subtract_mean=True, stream=None):
+    """Device series [T][C] -> fills the device tensors freq_out, spec_out (and acf_out).
+
+    Asynchronous on `stream`; uses the library's static scratch (no allocation)."""
+    S = _Buf(series, np.float64, "series")
+    F = _Buf(freq_out, np.float64, "freq_out", writable=True)
+    P = _Buf(spec_out, np.float64, "spec_out", writable=True)
+    A = _Buf(acf_out, np.float64, "acf_out", writable=True)
+    Tn, Cn = int(series.shape[0]), int(series.shape[1])
+    _check(_lib.tnep_spectrum_noalloc(S.ptr, Tn, Cn, float(dt_fs), int(kind), int(max_lag),
+                                      int(bool(subtract_mean)), F.ptr, P.ptr, A.ptr, _stream_ptr(stream)))
