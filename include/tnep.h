@@ -130,7 +130,8 @@ int tnep_output_dim(const tnep_ctx* ctx, int model);
 tnep_status tnep_eval(tnep_ctx* ctx, int n_frames, int n_atoms, const float* pos,
                       const float* box, const int* types, double* out, void* stream);
 
-/* Evaluates every model on `n_structs` structures of uneven size in one pass.
+/* Evaluates every model on `n_structs` structures of uneven size in one pass
+ * (fewer than 2^29 atoms in all).
  *   atom_offsets [n_structs + 1] (host memory), structure s owns atoms
  *                [atom_offsets[s], atom_offsets[s+1]); empty structures allowed
  *   pos [N][3], box [n_structs][3] (0 = open axis) or NULL, types [N]
@@ -214,7 +215,7 @@ enum {
   TNEP_OPT_FRAMES_PER_BATCH = 0,    /* frames per device pass in tnep_eval (0 = automatic) */
   TNEP_OPT_MAX_NEIGHBORS = 1,       /* hard cap on neighbours per atom (default 1024); lists grow up to it */
   TNEP_OPT_BLOCK_ATOMS = 2,         /* read-only: atoms per CTA of the fused kernel (128) */
-  TNEP_OPT_LAST_KERNEL_MS = 3,      /* read-only: device time of all fused-kernel launches of the last call (ms) */
+  TNEP_OPT_LAST_KERNEL_MS = 3,      /* read-only: device time of the tensor kernels (radial moments + fused) of the last call (ms) */
   TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2} (default 1) */
   TNEP_OPT_LAST_KERNEL_LAUNCHES = 5,/* read-only: fused-kernel launches in the last call */
   TNEP_OPT_LAST_NBR_MS = 6,         /* read-only: device time of the cell/neighbour pipeline in the last call (ms) */

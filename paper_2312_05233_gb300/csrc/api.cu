@@ -103,6 +103,9 @@ struct Model {
 struct Workspace {
   DevBuf<int> offsets, atom_struct, atom_cell, atom_slot, cell_count, cell_start, cell_atoms;
   DevBuf<int> sorted_orig, orig_sorted, sorted_struct, struct_cells, cnt_R, cnt_A, nbr_R, nbr_A;
+  DevBuf<int> nbr_tmp, seg_R;
+  DevBuf<float> mom;        // radial moments [slots][atom_stride]
+  int mom_v0 = -1, mom_w0 = -1;
   DevBuf<float4> pos4;
   DevBuf<StructGrid> grids;
   DevBuf<StructBox> boxes;
@@ -118,9 +121,10 @@ struct Workspace {
   void release() {
     for (auto* b : {&offsets, &atom_struct, &atom_cell, &atom_slot, &cell_count, &cell_start, &cell_atoms,
                     &sorted_orig, &orig_sorted, &sorted_struct, &struct_cells, &cnt_R, &cnt_A, &nbr_R, &nbr_A,
-                    &types_stage})
+                    &types_stage, &nbr_tmp, &seg_R})
       b->release();
     pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release(); partial.release();
+    mom.release();
     pos_stage[0].release(); pos_stage[1].release(); box_stage.release();
   }
 };
@@ -267,7 +271,9 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   TNEP_CUDA(w.cell_count.ensure(w.cells_cap + 1));
   TNEP_CUDA(w.cell_start.ensure(w.cells_cap + 1));
   TNEP_CUDA(w.nbr_R.ensure((size_t)stride * w.cap_R));
+  TNEP_CUDA(w.nbr_tmp.ensure((size_t)stride * w.cap_R));
   TNEP_CUDA(w.nbr_A.ensure((size_t)stride * w.cap_A));
+  TNEP_CUDA(w.seg_R.ensure((size_t)stride * c->n_types));
   TNEP_CUDA(cudaMemcpyAsync(w.offsets.p, h_offsets, sizeof(int) * (S + 1), cudaMemcpyHostToDevice, st));
   TNEP_CUDA(cudaMemsetAsync(w.cell_count.p, 0, sizeof(int) * (w.cells_cap + 1), st));
   NbrArgs a{};
@@ -297,6 +303,9 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   a.pos4 = w.pos4.p;
   a.nbr_R = w.nbr_R.p;
   a.nbr_A = w.nbr_A.p;
+  a.nbr_tmp = w.nbr_tmp.p;
+  a.seg_R = w.seg_R.p;
+  a.seg_stride = stride;
   a.cnt_R = w.cnt_R.p;
   a.cnt_A = w.cnt_A.p;
   a.cap_R = w.cap_R;
@@ -307,6 +316,41 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   return TNEP_OK;
 }
 
+// Radial moments of the lists in the workspace (F always; V for rank-1 and W
+// for rank-2 models).
+tnep_status compute_moments(tnep_ctx* c, cudaStream_t st, int N, bool need_v, bool need_w) {
+  Workspace& w = c->ws;
+  const int T = c->n_types;
+  const int per = T * kMomBasis;
+  w.mom_v0 = need_v ? per : -1;
+  w.mom_w0 = need_w ? per * (need_v ? 4 : 1) : -1;
+  const int slots = per * (1 + (need_v ? 3 : 0) + (need_w ? 6 : 0));
+  TNEP_CUDA(w.mom.ensure((size_t)slots * w.atom_stride));
+  RadialArgs r{};
+  r.n_atoms = N;
+  r.n_types = T;
+  r.pos4 = w.pos4.p;
+  r.sorted_struct = w.sorted_struct.p;
+  r.boxes = w.boxes.p;
+  r.nbr_R = w.nbr_R.p;
+  r.cap_R = w.cap_R;
+  r.seg_R = w.seg_R.p;
+  r.seg_stride = w.atom_stride;
+  r.rc_R = c->rc_R;
+  r.mom = w.mom.p;
+  r.mom_stride = w.atom_stride;
+  r.v0 = w.mom_v0;
+  r.w0 = w.mom_w0;
+  TNEP_CUDA(launch_radial_moments(r, st));
+  return TNEP_OK;
+}
+
+bool any_rank(const tnep_ctx* c, int rank) {
+  for (const auto& m : c->models)
+    if (m.d.rank == rank) return true;
+  return false;
+}
+
 FusedArgs fused_args(tnep_ctx* c, const Model& m, int N) {
   Workspace& w = c->ws;
   FusedArgs f{};
@@ -314,9 +358,10 @@ FusedArgs fused_args(tnep_ctx* c, const Model& m, int N) {
   f.pos4 = w.pos4.p;
   f.sorted_struct = w.sorted_struct.p;
   f.boxes = w.boxes.p;
-  f.nbr_R = w.nbr_R.p;
-  f.cnt_R = w.cnt_R.p;
-  f.cap_R = w.cap_R;
+  f.mom = w.mom.p;
+  f.mom_stride = w.atom_stride;
+  f.v0 = w.mom_v0;
+  f.w0 = w.mom_w0;
   f.nbr_A = w.nbr_A.p;
   f.cnt_A = w.cnt_A.p;
   f.cap_A = w.cap_A;
@@ -368,6 +413,7 @@ tnep_status run_models(tnep_ctx* c, cudaStream_t st, int S, int N, cudaEvent_t e
   const size_t per_model = (size_t)9 * w.atom_stride;
   TNEP_CUDA(w.per_atom.ensure(per_model * c->models.size()));
   TNEP_CUDA(w.out.ensure((size_t)std::max(S, 1) * total_C(c)));
+  TNEP_TRY(compute_moments(c, st, N, any_rank(c, 1), any_rank(c, 2)));
   for (size_t k = 0; k < c->models.size(); ++k) {
     const Model& m = c->models[k];
     FusedArgs f = fused_args(c, m, N);
@@ -443,7 +489,7 @@ cudaStream_t pick_stream(tnep_ctx* c, void* stream) {
 }
 
 int default_frames_per_batch(int n_atoms, int n_frames) {
-  const long long target = 1 << 19;  // ~0.5 M atoms per pass: >= 10 waves of 304 CTAs
+  const long long target = 1 << 20;  // ~1 M atoms per pass: >= 20 waves of 304 CTAs
   long long fb = std::max<long long>(1, target / std::max(n_atoms, 1));
   return (int)std::min<long long>(fb, std::max(n_frames, 1));
 }
@@ -612,6 +658,8 @@ tnep_status tnep_eval(tnep_ctx* c, int n_frames, int n_atoms, const float* pos, 
   const int Ctot = total_C(c);
   int fb = c->frames_per_batch > 0 ? std::min(c->frames_per_batch, n_frames)
                                    : default_frames_per_batch(n_atoms, n_frames);
+  if (n_atoms >= kMaxBatchAtoms) return fail(TNEP_ERR_INVALID, "a frame must hold fewer than 2^29 atoms");
+  fb = std::max(1, std::min(fb, (kMaxBatchAtoms - 1) / std::max(n_atoms, 1)));
   const bool pos_dev = is_device_ptr(pos);
   const bool box_dev = box && is_device_ptr(box);
   const bool out_dev = is_device_ptr(out);
@@ -684,7 +732,7 @@ tnep_status tnep_eval_batch(tnep_ctx* c, int n_structs, const int* atom_offsets,
   for (int s = 0; s < n_structs; ++s)
     if (atom_offsets[s + 1] < atom_offsets[s]) return fail(TNEP_ERR_INVALID, "atom_offsets must not decrease");
   const int N = atom_offsets[n_structs];
-  if (N > (1 << 30)) return fail(TNEP_ERR_INVALID, "too many atoms");
+  if (N >= kMaxBatchAtoms) return fail(TNEP_ERR_INVALID, "a batch must hold fewer than 2^29 atoms");
   if (N > 0 && (!pos || !types)) return fail(TNEP_ERR_INVALID, "NULL buffer");
   TNEP_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = pick_stream(c, stream);
@@ -752,6 +800,7 @@ tnep_status tnep_neighbors(tnep_ctx* c, int n_structs, const int* atom_offsets, 
     if (atom_offsets[s + 1] < atom_offsets[s]) return fail(TNEP_ERR_INVALID, "atom_offsets must not decrease");
   const int N = atom_offsets[n_structs];
   if (N == 0) return TNEP_OK;
+  if (N >= kMaxBatchAtoms) return fail(TNEP_ERR_INVALID, "a batch must hold fewer than 2^29 atoms");
   if (!pos) return fail(TNEP_ERR_INVALID, "pos is NULL");
   TNEP_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = pick_stream(c, stream);
@@ -808,6 +857,7 @@ tnep_status tnep_eval_population(tnep_ctx* c, int model, int n_pop, const float*
   for (int s = 0; s < n_structs; ++s)
     if (atom_offsets[s + 1] < atom_offsets[s]) return fail(TNEP_ERR_INVALID, "atom_offsets must not decrease");
   const int N = atom_offsets[n_structs];
+  if (N >= kMaxBatchAtoms) return fail(TNEP_ERR_INVALID, "a batch must hold fewer than 2^29 atoms");
   if (N > 0 && (!pos || !types)) return fail(TNEP_ERR_INVALID, "NULL buffer");
   TNEP_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = pick_stream(c, stream);
@@ -838,6 +888,10 @@ tnep_status tnep_eval_population(tnep_ctx* c, int model, int n_pop, const float*
     TNEP_CUDA(w.per_atom.ensure(pa_pop * n_pop));
     TNEP_CUDA(w.out.ensure((size_t)n_pop * n_structs * m.C));
     TNEP_CUDA(c->pop_rmse.ensure(n_pop));
+    cudaEvent_t* ev0 = nullptr;
+    TNEP_TRY(pass_events(c, 0, &ev0));
+    TNEP_CUDA(cudaEventRecord(ev0[1], st));
+    TNEP_TRY(compute_moments(c, st, N, m.d.rank == 1, m.d.rank == 2));
     FusedArgs f = fused_args(c, m, N);
     f.model = c->pop_params.p;
     f.model_stride = m.lay.words;
@@ -845,7 +899,6 @@ tnep_status tnep_eval_population(tnep_ctx* c, int model, int n_pop, const float*
     f.per_atom_stride = pa_pop;
     cudaEvent_t* ev = nullptr;
     TNEP_TRY(pass_events(c, 0, &ev));
-    TNEP_CUDA(cudaEventRecord(ev[1], st));
     TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, n_pop, st));
     TNEP_CUDA(cudaEventRecord(ev[2], st));
     TNEP_CUDA(w.partial.ensure((size_t)n_pop * n_structs * reduce_chunks(w.max_atoms) * m.C));

@@ -247,6 +247,11 @@ __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL
   return d;
 }
 
+// One thread per atom.  Radial entries go to a scratch list tagged with the
+// neighbour type (bits 29-31), then the same thread counting-sorts its own
+// entries by type into the final radial list (stable: ascending scan order
+// inside each type) and records the per-type counts; the radial moments
+// kernel walks one type segment at a time.
 __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell, float rc2R, float rc2A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_atoms) return;
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
           const float dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
           const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
           if (r2 < rc2R && j != i) {
-            if (cR < a.cap_R) a.nbr_R[nbr_index(i, cR, a.cap_R)] = j;
+            if (cR < a.cap_R) a.nbr_tmp[nbr_index(i, cR, a.cap_R)] = j | (__float_as_int(pj.w) << kTypeShift);
             ++cR;
             if (r2 < rc2A) {
               if (cA < a.cap_A) a.nbr_A[nbr_index(i, cA, a.cap_A)] = j;
@@ -289,6 +294,32 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   a.cnt_A[i] = cA;
   if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
   if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
+  // counting sort of the radial entries by neighbour type
+  const int n = min(cR, a.cap_R);
+  int cnt[kMaxTypes];
+#pragma unroll
+  for (int u = 0; u < kMaxTypes; ++u) cnt[u] = 0;
+  for (int e = 0; e < n; ++e) {
+    const int t = (unsigned)a.nbr_tmp[nbr_index(i, e, a.cap_R)] >> kTypeShift;
+#pragma unroll
+    for (int u = 0; u < kMaxTypes; ++u) cnt[u] += (t == u);
+  }
+  int off[kMaxTypes];
+  int run = 0;
+#pragma unroll
+  for (int u = 0; u < kMaxTypes; ++u) { off[u] = run; run += cnt[u]; }
+  for (int e = 0; e < n; ++e) {
+    const int v = a.nbr_tmp[nbr_index(i, e, a.cap_R)];
+    const int t = (unsigned)v >> kTypeShift;
+    int dst = 0;
+#pragma unroll
+    for (int u = 0; u < kMaxTypes; ++u)
+      if (t == u) { dst = off[u]; off[u] = dst + 1; }
+    a.nbr_R[nbr_index(i, dst, a.cap_R)] = v & kIndexMask;
+  }
+#pragma unroll
+  for (int u = 0; u < kMaxTypes; ++u)
+    if (u < a.n_types) a.seg_R[(size_t)u * a.seg_stride + i] = cnt[u];
 }
 
 __global__ void k_export(int n, const int* sorted_orig, const int* nbr_R, const int* cnt_R, int cap_R,

@@ -1,0 +1,94 @@
+// Radial moments: one pass over each atom's type-sorted radial list.
+//
+// g_n^{t_i t_j}(r) = sum_k c^{t_i t_j}_{nk} f_k(r) is linear in c, so the
+// radial descriptor and the radial part of Eqs. 3-4 need only per-type sums
+// of basis values over the neighbours, computed once per frame and shared by
+// every model (and every individual of a population) with the same rc_R:
+//   F^t_k    = sum_{j of type t} f_k(r_ij)
+//   V^t_k    = sum_j r_ij f_k'(r_ij) r_ij_vec                 (rank 1)
+//   W^t_k    = sum_j f_k'(r_ij) / r_ij  r_ij_vec (x) r_ij_vec  (rank 2, symmetric)
+// since -|r|^2 dU_i/dr_ij = -r g'(r) r_vec and -r_vec (x) dU_i/dr_ij =
+// -g'(r)/r r_vec (x) r_vec with g' = sum_k D_k f_k'.
+
+#include "tnep_device.cuh"
+#include "tnep_internal.cuh"
+
+namespace tnep {
+
+namespace {
+
+template <bool HV, bool HW>
+__global__ void __launch_bounds__(128) k_radial(const __grid_constant__ RadialArgs a) {
+  constexpr int B = kMomBasis;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_atoms) return;
+  const float4 pi = a.pos4[i];
+  const StructBox bx = a.boxes[a.sorted_struct[i]];
+  const float rcinv = 1.f / a.rc_R;
+  float* mom = a.mom + i;
+  const size_t ms = a.mom_stride;
+  int start = 0;
+  for (int t = 0; t < a.n_types; ++t) {
+    const int n = a.seg_R[(size_t)t * a.seg_stride + i];
+    float F[B], V[HV ? 3 * B : 1], W[HW ? 6 * B : 1];
+#pragma unroll
+    for (int k = 0; k < B; ++k) F[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < (HV ? 3 * B : 1); ++k) V[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < (HW ? 6 * B : 1); ++k) W[k] = 0.f;
+    NbrWalk w(a.nbr_R, a.pos4, i, a.cap_R, start, n, pi);
+    for (int kk = 0; kk < n; ++kk) {
+      const float4 pj = w.next(kk);
+      const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
+      const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
+      const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv;
+      float f[B], df[B];
+      basis_fwd_bwd<B>(r, rcinv, f, df);
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        F[k] += f[k];
+        if constexpr (HV) {
+          const float s = r * df[k];
+          V[3 * k] += s * dx; V[3 * k + 1] += s * dy; V[3 * k + 2] += s * dz;
+        }
+        if constexpr (HW) {
+          const float s = df[k] * rinv;
+          const float sx = s * dx, sy = s * dy;
+          W[6 * k] += sx * dx; W[6 * k + 1] += sx * dy; W[6 * k + 2] += sx * dz;
+          W[6 * k + 3] += sy * dy; W[6 * k + 4] += sy * dz; W[6 * k + 5] += s * dz * dz;
+        }
+      }
+    }
+    start += n;
+#pragma unroll
+    for (int k = 0; k < B; ++k) mom[(size_t)(t * B + k) * ms] = F[k];
+    if constexpr (HV) {
+#pragma unroll
+      for (int k = 0; k < 3 * B; ++k) mom[(size_t)(a.v0 + 3 * t * B + k) * ms] = V[k];
+    }
+    if constexpr (HW) {
+#pragma unroll
+      for (int k = 0; k < 6 * B; ++k) mom[(size_t)(a.w0 + 6 * t * B + k) * ms] = W[k];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_radial_moments(const RadialArgs& a, cudaStream_t st) {
+  if (a.n_atoms <= 0) return cudaSuccess;
+  count_launches(1);
+  const int grid = (a.n_atoms + 127) / 128;
+  const bool hv = a.v0 >= 0, hw = a.w0 >= 0;
+  if (hv && hw) k_radial<true, true><<<grid, 128, 0, st>>>(a);
+  else if (hv) k_radial<true, false><<<grid, 128, 0, st>>>(a);
+  else if (hw) k_radial<false, true><<<grid, 128, 0, st>>>(a);
+  else k_radial<false, false><<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tnep

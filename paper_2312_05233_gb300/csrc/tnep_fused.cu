@@ -1,21 +1,21 @@
 // Fused TNEP kernel: descriptor -> network -> partial forces -> tensor contraction.
 //
-// One thread owns one atom i and walks its neighbour lists four times:
-//   1. radial forward   q_n   = sum_j g^R_n(r_ij)
+// One thread owns one atom i:
+//   1. radial descriptor q_n = sum_{t,k} c^{t_i t}_{nk} F^t_k from the per-type
+//      radial moments (radial.cu; g_n is linear in c)
 //   2. angular forward  A_nlm = sum_j g^A_n(r_ij) p_lm(u_ij)   (120 register accumulators)
 //      then q_nl = sum_m w_lm A_nlm^2 and the 4-body invariant
 //   3. network U_i = w1 . tanh(W0 s - b0) - b1 and dU/dq (Eq. 1)
-//   4. angular backward: partial force
+//   4. radial part of the contraction through the moments V (rank 1) or W (rank 2)
+//   5. angular backward: partial force
 //        dU_i/dr_ij = s1 u + (V - (u.V) u) / r,
 //        s1 = sum_lm T_lm p_lm,  V = sum_lm S_lm grad p_lm,
 //        S_lm = sum_n G_nlm g_n(r),  T_lm = sum_n G_nlm g_n'(r),  G = dU/dA
-//   5. radial backward: dU_i/dr_ij = (sum_k D^{t_j}_k f_k'(r)) u,
-//        D^t_k = sum_n (dU/dq_n) c^{t_i t}_{nk}
-// and contracts each partial force on the fly (Sec. II.B-C):
+// and contracts each angular partial force on the fly (Sec. II.B-C):
 //   rank 1 (Eq. 3):  mu_i    -= |r_ij|^2 dU_i/dr_ij
 //   rank 2 (Eq. 4):  alpha_i -= r_ij (x) dU_i/dr_ij,  plus U_i on the diagonal.
-// Nothing per pair is stored: basis values are recomputed in the backward
-// walks.  Per-atom results go out in float32 (SoA) and are summed per
+// Nothing per pair is stored: angular basis values are recomputed in the
+// backward walk.  Per-atom results go out in float32 (SoA) and are summed per
 // structure in float64 by the reduce kernel.
 //
 // Angular functions: real Cartesian polynomials p_lm(u) of the unit vector u
@@ -30,13 +30,13 @@
 
 #include <atomic>
 
+#include "tnep_device.cuh"
 #include "tnep_internal.cuh"
 
 namespace tnep {
 
 namespace {
 
-constexpr float kPi = 3.14159265358979323846f;
 // (2 2 2; 0 0 0) = -sqrt(2/35);  C4 = -sqrt(2/35) * (5/(4 pi))^1.5 * 9/2
 constexpr float kC4 = -0.26998130975990770f;
 
@@ -149,50 +149,6 @@ __device__ __forceinline__ void harmonic_grad(const float* S, float x, float y, 
   }
 }
 
-// Chebyshev basis f_k = (T_k(x) + 1) f_c / 2, x = 2 (r/rc - 1)^2 - 1.
-template <int B>
-__device__ __forceinline__ void basis_fwd(float r, float rcinv, float* f) {
-  float sn, cs;
-  __sincosf(kPi * r * rcinv, &sn, &cs);
-  const float fc = 0.5f + 0.5f * cs;
-  const float t = r * rcinv - 1.f;
-  const float x = 2.f * t * t - 1.f;
-  const float hfc = 0.5f * fc;
-  f[0] = fc;
-  float T0 = 1.f, T1 = x;
-  if constexpr (B > 1) f[1] = hfc * (x + 1.f);
-#pragma unroll
-  for (int k = 2; k < B; ++k) {
-    const float T2 = 2.f * x * T1 - T0;
-    f[k] = hfc * (T2 + 1.f);
-    T0 = T1; T1 = T2;
-  }
-}
-
-// Basis and its radial derivative.
-template <int B>
-__device__ __forceinline__ void basis_fwd_bwd(float r, float rcinv, float* f, float* df) {
-  float sn, cs;
-  __sincosf(kPi * r * rcinv, &sn, &cs);
-  const float fc = 0.5f + 0.5f * cs;
-  const float dfc = -0.5f * kPi * rcinv * sn;
-  const float t = r * rcinv - 1.f;
-  const float x = 2.f * t * t - 1.f;
-  const float dx = 4.f * t * rcinv;
-  const float hfc = 0.5f * fc, hdfc = 0.5f * dfc, hdxfc = 0.5f * dx * fc;
-  f[0] = fc; df[0] = dfc;
-  float T0 = 1.f, T1 = x, dT0 = 0.f, dT1 = 1.f;
-  if constexpr (B > 1) { f[1] = hfc * (x + 1.f); df[1] = hdxfc + hdfc * (x + 1.f); }
-#pragma unroll
-  for (int k = 2; k < B; ++k) {
-    const float T2 = 2.f * x * T1 - T0;
-    const float dT2 = 2.f * T1 + 2.f * x * dT1 - dT0;
-    f[k] = hfc * (T2 + 1.f);
-    df[k] = hdxfc * dT2 + hdfc * (T2 + 1.f);
-    T0 = T1; T1 = T2; dT0 = dT1; dT1 = dT2;
-  }
-}
-
 // Loads one (t_i, t_j) coefficient block c[n][k] from shared memory.
 template <int NN, int B>
 __device__ __forceinline__ void load_coeffs(const float* blk, float* cc) {
@@ -204,45 +160,6 @@ __device__ __forceinline__ void load_coeffs(const float* blk, float* cc) {
     cc[4 * v] = t.x; cc[4 * v + 1] = t.y; cc[4 * v + 2] = t.z; cc[4 * v + 3] = t.w;
   }
 }
-
-// Minimum-image component of r_ij = r_j - r_i.  The image shift k is taken
-// from the plain difference; the box edge is then subtracted from the operand
-// that lies near the far face before the final difference, which is exact
-// (Sterbenz) for positions wrapped into [0, L): pairs across a face keep the
-// precision of short vectors instead of rounding at ulp(L).
-__device__ __forceinline__ float min_image(float xj, float xi, float L, float invL) {
-  if (L > 0.f) {
-    const float k = rintf((xj - xi) * invL);
-    const float aj = fmaf(-fmaxf(k, 0.f), L, xj);
-    const float ai = fmaf(-fmaxf(-k, 0.f), L, xi);
-    return aj - ai;
-  }
-  return xj - xi;
-}
-
-// Software-pipelined walk over one atom's neighbour list: the neighbour index
-// is fetched two iterations ahead and its position one iteration ahead, so
-// the dependent index -> position gather overlaps the current pair's math.
-// Out-of-range slots re-use a valid index (loads stay in bounds).
-struct NbrWalk {
-  const int* __restrict__ list;
-  const float4* __restrict__ pos;
-  int i, cap, n;
-  int j_ahead;
-  float4 p_ahead;
-  __device__ __forceinline__ NbrWalk(const int* l, const float4* p, int i_, int cap_, int n_, float4 self)
-      : list(l), pos(p), i(i_), cap(cap_), n(n_) {
-    const int j0 = n > 0 ? list[nbr_index(i, 0, cap)] : i;
-    j_ahead = n > 1 ? list[nbr_index(i, 1, cap)] : j0;
-    p_ahead = n > 0 ? pos[j0] : self;
-  }
-  __device__ __forceinline__ float4 next(int k) {
-    const float4 pj = p_ahead;
-    p_ahead = pos[j_ahead];
-    if (k + 2 < n) j_ahead = list[nbr_index(i, k + 2, cap)];
-    return pj;
-  }
-};
 
 // Tr(M^3) of the traceless symmetric M built from the l=2 sums a[0..4]
 // (xy, yz, xz, x^2-y^2, 3z^2-1), and its gradient with respect to a.
@@ -293,33 +210,25 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
   const int ti = __float_as_int(pi.w);
   const StructBox bx = a.boxes[a.sorted_struct[i]];
   const int T = Ly.n_types;
-  const float rcRinv = 1.f / a.rc_R, rcAinv = 1.f / a.rc_A;
+  const float rcAinv = 1.f / a.rc_A;
 
-  // ---------------------------------------------------------------- radial forward
+  // ---------------------------------------------------------------- radial descriptor
+  // q_n = sum_t sum_k c^{t_i t}_{nk} F^t_k from the per-type radial moments
   float q[DP];
 #pragma unroll
   for (int d = 0; d < DP; ++d) q[d] = 0.f;
-  const int nR = min(a.cnt_R[i], a.cap_R);
   const float* cR_i = sm + Ly.off_cR + ti * T * Ly.stride_cR;
-  NbrWalk wR(a.nbr_R, a.pos4, i, a.cap_R, nR, pi);
-  for (int kk = 0; kk < nR; ++kk) {
-    const float4 pj = wR.next(kk);
-    const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
-    const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
-    const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float r = r2 * rsqrtf(r2);
-    float f[BR];
-    basis_fwd<BR>(r, rcRinv, f);
+  const float* mom = a.mom + i;
+  for (int t = 0; t < T; ++t) {
+    float Fk[BR];
+#pragma unroll
+    for (int k = 0; k < BR; ++k) Fk[k] = mom[(size_t)(t * kMomBasis + k) * a.mom_stride];
     float cc[NBR4];
-    load_coeffs<NR, BR>(cR_i + __float_as_int(pj.w) * Ly.stride_cR, cc);
+    load_coeffs<NR, BR>(cR_i + t * Ly.stride_cR, cc);
 #pragma unroll
-    for (int n = 0; n < NR; ++n) {
-      float g = 0.f;
+    for (int n = 0; n < NR; ++n)
 #pragma unroll
-      for (int k = 0; k < BR; ++k) g += cc[n * BR + k] * f[k];
-      q[n] += g;
-    }
+      for (int k = 0; k < BR; ++k) q[n] += cc[n * BR + k] * Fk[k];
   }
 
   // ---------------------------------------------------------------- angular forward
@@ -329,7 +238,7 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
     float A[NA * NLM];
 #pragma unroll
     for (int k = 0; k < NA * NLM; ++k) A[k] = 0.f;
-    NbrWalk wA(a.nbr_A, a.pos4, i, a.cap_A, nA, pi);
+    NbrWalk wA(a.nbr_A, a.pos4, i, a.cap_A, 0, nA, pi);
     for (int kk = 0; kk < nA; ++kk) {
       const float4 pj = wA.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
@@ -411,6 +320,36 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
 #pragma unroll
   for (int c = 0; c < C; ++c) acc[c] = 0.f;
 
+  // ---------------------------------------------------------------- radial part of Eqs. 3-4
+  // dU_i/dr_ij (radial) = (sum_k D^{t_j}_k f_k'(r)) r_ij / r with
+  // D^t_k = sum_n (dU/dq_n) c^{t_i t}_{nk}; contracted through the moments:
+  //   rank 1: mu_i    -= sum_{t,k} D^t_k V^t_k
+  //   rank 2: alpha_i -= sum_{t,k} D^t_k W^t_k
+  for (int t = 0; t < T; ++t) {
+    float cc[NBR4];
+    load_coeffs<NR, BR>(cR_i + t * Ly.stride_cR, cc);
+#pragma unroll
+    for (int k = 0; k < BR; ++k) {
+      float Dk = 0.f;
+#pragma unroll
+      for (int n = 0; n < NR; ++n) Dk += e[n] * cc[n * BR + k];
+      const int tk = t * kMomBasis + k;
+      if constexpr (RANK == 1) {
+        const float* v = mom + (size_t)(a.v0 + 3 * tk) * a.mom_stride;
+        acc[0] -= Dk * v[0];
+        acc[1] -= Dk * v[(size_t)a.mom_stride];
+        acc[2] -= Dk * v[2 * (size_t)a.mom_stride];
+      } else {
+        const float* w = mom + (size_t)(a.w0 + 6 * tk) * a.mom_stride;
+        const size_t ms = a.mom_stride;
+        const float wxx = w[0], wxy = w[ms], wxz = w[2 * ms], wyy = w[3 * ms], wyz = w[4 * ms], wzz = w[5 * ms];
+        acc[0] -= Dk * wxx; acc[1] -= Dk * wxy; acc[2] -= Dk * wxz;
+        acc[3] -= Dk * wxy; acc[4] -= Dk * wyy; acc[5] -= Dk * wyz;
+        acc[6] -= Dk * wxz; acc[7] -= Dk * wyz; acc[8] -= Dk * wzz;
+      }
+    }
+  }
+
   // ---------------------------------------------------------------- angular backward
   {
     float G[NA * NLM];
@@ -429,7 +368,7 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
         for (int m = 0; m < 5; ++m) G[n * NLM + 3 + m] += e4 * gr[m];
       }
     }
-    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, nA, pi);
+    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, 0, nA, pi);
     for (int kk = 0; kk < nA; ++kk) {
       const float4 pj = wB.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
@@ -476,44 +415,6 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
         acc[3] -= dy * fx; acc[4] -= dy * fy; acc[5] -= dy * fz;
         acc[6] -= dz * fx; acc[7] -= dz * fy; acc[8] -= dz * fz;
       }
-    }
-  }
-
-  // ---------------------------------------------------------------- radial backward
-  for (int t = 0; t < T; ++t) {
-    float cc[NBR4];
-    load_coeffs<NR, BR>(cR_i + t * Ly.stride_cR, cc);
-#pragma unroll
-    for (int k = 0; k < BR; ++k) {
-      float v = 0.f;
-#pragma unroll
-      for (int n = 0; n < NR; ++n) v += e[n] * cc[n * BR + k];
-      scratch[(t * BR + k) * kFusedBlock] = v;
-    }
-  }
-  NbrWalk wS(a.nbr_R, a.pos4, i, a.cap_R, nR, pi);
-  for (int kk = 0; kk < nR; ++kk) {
-    const float4 pj = wS.next(kk);
-    const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
-    const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
-    const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    float f[BR], df[BR];
-    basis_fwd_bwd<BR>(r, rcRinv, f, df);
-    const float* Dt = scratch + __float_as_int(pj.w) * BR * kFusedBlock;
-    float gs = 0.f;
-#pragma unroll
-    for (int k = 0; k < BR; ++k) gs += Dt[k * kFusedBlock] * df[k];
-    const float fs = gs * rinv;  // dU/dr_ij = gs * u = gs * d / r
-    if constexpr (RANK == 1) {
-      const float w = -r2 * fs;
-      acc[0] += w * dx; acc[1] += w * dy; acc[2] += w * dz;
-    } else {
-      acc[0] -= dx * dx * fs; acc[1] -= dx * dy * fs; acc[2] -= dx * dz * fs;
-      acc[3] -= dy * dx * fs; acc[4] -= dy * dy * fs; acc[5] -= dy * dz * fs;
-      acc[6] -= dz * dx * fs; acc[7] -= dz * dy * fs; acc[8] -= dz * dz * fs;
     }
   }
 
@@ -629,8 +530,6 @@ size_t fused_smem_bytes(int variant, const ModelLayout& lay) {
   int slots = 0;
   if (variant == kVarStd) slots = 5 * 24;
   if (variant == kVarSmall) slots = 3 * 15;
-  const int bR = variant == kVarStd ? 9 : 7;
-  slots = slots > lay.n_types * bR ? slots : lay.n_types * bR;
   return (size_t)(lay.words + slots * kFusedBlock) * sizeof(float);
 }
 

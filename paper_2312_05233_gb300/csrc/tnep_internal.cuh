@@ -10,6 +10,12 @@ namespace tnep {
 
 constexpr int kMaxTypes = 8;
 constexpr int kFusedBlock = 128;  // atoms per CTA of the fused kernel (one atom per thread)
+// Radial scratch entries carry the neighbour type in bits 29-31, so a batch
+// holds fewer than 2^29 atoms.
+constexpr int kTypeShift = 29;
+constexpr int kIndexMask = (1 << kTypeShift) - 1;
+constexpr int kMaxBatchAtoms = 1 << kTypeShift;
+constexpr int kMomBasis = 9;  // radial moments are computed for k = 0..8 (basis_R <= 8)
 
 // Device-side status word, reset before each batch and read back after it.
 struct DevStatus {
@@ -68,7 +74,10 @@ struct NbrArgs {
   int* orig_sorted;         // [N] input -> sorted index
   int* sorted_struct;       // [N]
   float4* pos4;             // [N] sorted positions, w = type bits
-  int* nbr_R; int* nbr_A;   // warp-tiled lists (sorted indices)
+  int* nbr_R; int* nbr_A;   // warp-tiled lists (sorted indices); radial sorted by neighbour type
+  int* nbr_tmp;             // radial scratch (type-tagged), same layout as nbr_R
+  int* seg_R;               // [n_types][seg_stride] radial neighbours of each type
+  int seg_stride;
   int* cnt_R; int* cnt_A;   // [N] true counts (may exceed caps)
   int cap_R, cap_A;
   int cells_cap;
@@ -85,6 +94,25 @@ long long launches_total();
 // Launches the cell-list + neighbour pipeline on `st`.
 cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st);
 
+// Radial moments per atom and neighbour type t (SoA, slot-major, stride mom_stride):
+//   F^t_k     = sum_{j of type t} f_k(r_ij)                       slots  t*B + k
+//   V^t_k,a   = sum_j r_ij f_k'(r_ij) r_ij^a                      slots  v0 + (t*B + k)*3 + a
+//   W^t_k,ab  = sum_j f_k'(r_ij) / r_ij  r_ij^a r_ij^b  (ab in xx xy xz yy yz zz)  slots w0 + (t*B + k)*6 + c
+// with B = kMomBasis.  They hold everything the radial descriptor and the
+// radial part of Eqs. 3-4 need, for every model sharing rc_R.
+struct RadialArgs {
+  int n_atoms, n_types;
+  const float4* pos4;
+  const int* sorted_struct;
+  const StructBox* boxes;
+  const int* nbr_R; int cap_R;
+  const int* seg_R; int seg_stride;
+  float rc_R;
+  float* mom; int mom_stride;
+  int v0, w0;  // slot bases, -1 when not computed
+};
+cudaError_t launch_radial_moments(const RadialArgs& a, cudaStream_t st);
+
 // Packed model layout in device memory (floats).
 struct ModelLayout {
   int n_types, nets, H, D, Dp;
@@ -99,7 +127,7 @@ struct FusedArgs {
   const float4* pos4;
   const int* sorted_struct;
   const StructBox* boxes;
-  const int* nbr_R; const int* cnt_R; int cap_R;
+  const float* mom; int mom_stride; int v0, w0;   // radial moments (see RadialArgs)
   const int* nbr_A; const int* cnt_A; int cap_A;
   const float* model;        // packed model (first individual)
   size_t model_stride;       // floats between individuals (population), 0 otherwise
