@@ -103,7 +103,7 @@ struct Model {
 struct Workspace {
   DevBuf<int> offsets, atom_struct, atom_cell, atom_slot, cell_count, cell_start, cell_atoms;
   DevBuf<int> sorted_orig, orig_sorted, sorted_struct, struct_cells, cnt_R, cnt_A, nbr_R, nbr_A;
-  DevBuf<int> nbr_tmp, seg_R;
+  DevBuf<int> nbr_tmp, seg_R, struct_flags;
   DevBuf<float> mom;        // radial moments [slots][atom_stride]
   int mom_v0 = -1, mom_w0 = -1;
   DevBuf<float4> pos4;
@@ -121,7 +121,7 @@ struct Workspace {
   void release() {
     for (auto* b : {&offsets, &atom_struct, &atom_cell, &atom_slot, &cell_count, &cell_start, &cell_atoms,
                     &sorted_orig, &orig_sorted, &sorted_struct, &struct_cells, &cnt_R, &cnt_A, &nbr_R, &nbr_A,
-                    &types_stage, &nbr_tmp, &seg_R})
+                    &types_stage, &nbr_tmp, &seg_R, &struct_flags})
       b->release();
     pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release(); partial.release();
     mom.release();
@@ -256,6 +256,7 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   w.cap_A = c->cap_A;
   TNEP_CUDA(w.offsets.ensure(S + 1));
   TNEP_CUDA(w.struct_cells.ensure(S + 1));
+  TNEP_CUDA(w.struct_flags.ensure(S));
   TNEP_CUDA(w.grids.ensure(S));
   TNEP_CUDA(w.boxes.ensure(S));
   TNEP_CUDA(w.atom_struct.ensure(stride));
@@ -276,6 +277,7 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   TNEP_CUDA(w.seg_R.ensure((size_t)stride * c->n_types));
   TNEP_CUDA(cudaMemcpyAsync(w.offsets.p, h_offsets, sizeof(int) * (S + 1), cudaMemcpyHostToDevice, st));
   TNEP_CUDA(cudaMemsetAsync(w.cell_count.p, 0, sizeof(int) * (w.cells_cap + 1), st));
+  TNEP_CUDA(cudaMemsetAsync(w.struct_flags.p, 0, sizeof(int) * S, st));
   NbrArgs a{};
   a.n_structs = S;
   a.n_atoms = N;
@@ -291,6 +293,7 @@ tnep_status build_lists(tnep_ctx* c, cudaStream_t st, int S, const int* h_offset
   a.grids = w.grids.p;
   a.boxes = w.boxes.p;
   a.struct_cells = w.struct_cells.p;
+  a.struct_flags = w.struct_flags.p;
   a.atom_struct = w.atom_struct.p;
   a.atom_cell = w.atom_cell.p;
   a.atom_slot = w.atom_slot.p;

@@ -172,9 +172,14 @@ __global__ void k_bin(NbrArgs a) {
   const int s = lo;
   a.atom_struct[g] = s;
   const StructGrid G = a.grids[s];
-  const int c0 = cell_coord(a.pos[3 * (size_t)g + 0], G, 0);
-  const int c1 = cell_coord(a.pos[3 * (size_t)g + 1], G, 1);
-  const int c2 = cell_coord(a.pos[3 * (size_t)g + 2], G, 2);
+  const float x0 = a.pos[3 * (size_t)g + 0], x1 = a.pos[3 * (size_t)g + 1], x2 = a.pos[3 * (size_t)g + 2];
+  const int c0 = cell_coord(x0, G, 0);
+  const int c1 = cell_coord(x1, G, 1);
+  const int c2 = cell_coord(x2, G, 2);
+  const bool outside = (G.L[0] > 0.0f && !(x0 >= 0.0f && x0 < G.L[0])) ||
+                       (G.L[1] > 0.0f && !(x1 >= 0.0f && x1 < G.L[1])) ||
+                       (G.L[2] > 0.0f && !(x2 >= 0.0f && x2 < G.L[2]));
+  if (outside) atomicOr(&a.struct_flags[s], 1);
   const int cell = G.cell_offset + (c2 * G.nc[1] + c1) * G.nc[0] + c0;
   if (cell >= a.cells_cap) {  // unreachable: cells per structure <= 2n + 8
     raise_error(a.status, TNEP_ERR_INVALID, s);
@@ -225,17 +230,29 @@ __global__ void k_cell_sort(NbrArgs a, int* sorted_cell) {
   }
 }
 
-__device__ __forceinline__ int axis_cells(int c, int nc, bool periodic, int k, int* out) {
+// Stencil cells along one axis with their image shift (in units of the box
+// edge, as the float32 product L * k).  Periodic axes with at least 2k+1
+// cells wrap and carry the shift that the minimum-image rule would pick for
+// any pair within the cutoff; shorter periodic axes list every cell once and
+// leave the shift to rint (flagged by the return value < 0).
+__device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* cell, float* sh) {
   int n = 0;
-  if (periodic) {
+  if (L > 0.0f) {
     if (nc >= 2 * k + 1) {
-      for (int o = -k; o <= k; ++o) out[n++] = (c + o + nc) % nc;
+      for (int o = -k; o <= k; ++o) {
+        int cc = c + o;
+        float s = 0.0f;
+        if (cc < 0) { cc += nc; s = L; }
+        else if (cc >= nc) { cc -= nc; s = -L; }
+        cell[n] = cc; sh[n] = s; ++n;
+      }
     } else {
-      for (int o = 0; o < nc; ++o) out[n++] = o;
+      for (int o = 0; o < nc; ++o) { cell[n] = o; sh[n] = 0.0f; ++n; }
+      return -n;
     }
   } else {
     const int lo = max(0, c - k), hi = min(nc - 1, c + k);
-    for (int o = lo; o <= hi; ++o) out[n++] = o;
+    for (int o = lo; o <= hi; ++o) { cell[n] = o; sh[n] = 0.0f; ++n; }
   }
   return n;
 }
@@ -243,7 +260,7 @@ __device__ __forceinline__ int axis_cells(int c, int nc, bool periodic, int k, i
 // Minimum-image difference with every operation rounded separately.
 __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
   float d = __fsub_rn(xj, xi);
-  if (L > 0.0f) d = __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, invL))));
+  d = __fsub_rn(d, __fmul_rn(L, rintf(__fmul_rn(d, invL))));
   return d;
 }
 
@@ -262,30 +279,51 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   const int cx = lc % G.nc[0], cy = (lc / G.nc[0]) % G.nc[1], cz = lc / (G.nc[0] * G.nc[1]);
   int lx[5], ly[5], lz[5];
   const int k = a.cell_div;
-  const int nx = axis_cells(cx, G.nc[0], G.L[0] > 0.0f, k, lx);
-  const int ny = axis_cells(cy, G.nc[1], G.L[1] > 0.0f, k, ly);
-  const int nz = axis_cells(cz, G.nc[2], G.L[2] > 0.0f, k, lz);
+  int xc[5], yc[5], zc[5];
+  float xs[5], ys[5], zs[5];
+  int nx = axis_stencil(cx, G.nc[0], G.L[0], k, xc, xs);
+  int ny = axis_stencil(cy, G.nc[1], G.L[1], k, yc, ys);
+  int nz = axis_stencil(cz, G.nc[2], G.L[2], k, zc, zs);
+  // The shift of a stencil cell equals L * rint((p_j - p_i) / L) for every pair
+  // the cutoff can accept when all coordinates lie in [0, L); otherwise (or
+  // when an axis has too few cells to carry shifts) use rint per pair.  Both
+  // give the float32 rule of the header bit for bit.
+  const bool use_rint = nx < 0 || ny < 0 || nz < 0 || (a.struct_flags[s] & 1);
+  nx = abs(nx); ny = abs(ny); nz = abs(nz);
+  int* wR = a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
+  int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
   int cR = 0, cA = 0;
   for (int iz = 0; iz < nz; ++iz) {
     for (int iy = 0; iy < ny; ++iy) {
-      const int row = G.cell_offset + (lz[iz] * G.nc[1] + ly[iy]) * G.nc[0];
-      for (int ix = 0; ix < nx; ++ix) {
-        const int gc = row + lx[ix];
-        const int j0 = a.cell_start[gc], j1 = a.cell_start[gc + 1];
+      const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
+      const float sy = ys[iy], sz = zs[iz];
+      int ix = 0;
+      while (ix < nx) {
+        // merge x-cells that are contiguous and share a shift into one range
+        int ie = ix + 1;
+        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) ++ie;
+        const float sx = xs[ix];
+        const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
+        ix = ie;
         for (int j = j0; j < j1; ++j) {
           const float4 pj = a.pos4[j];
-          const float dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
-          const float dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
-          const float dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
-          const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-          if (r2 < rc2R && j != i) {
-            if (cR < a.cap_R) a.nbr_tmp[nbr_index(i, cR, a.cap_R)] = j | (__float_as_int(pj.w) << kTypeShift);
-            ++cR;
-            if (r2 < rc2A) {
-              if (cA < a.cap_A) a.nbr_A[nbr_index(i, cA, a.cap_A)] = j;
-              ++cA;
-            }
+          float dx, dy, dz;
+          if (!use_rint) {
+            dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
+            dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
+            dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
+          } else {
+            dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
+            dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
+            dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
           }
+          const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+          const bool inR = (r2 < rc2R) && (j != i);
+          if (inR && cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(pj.w) << kTypeShift);
+          cR += inR;
+          const bool inA = inR && (r2 < rc2A);
+          if (inA && cA < a.cap_A) wA[(size_t)cA * 32] = j;
+          cA += inA;
         }
       }
     }

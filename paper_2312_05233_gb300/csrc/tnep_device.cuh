@@ -70,6 +70,8 @@ __device__ __forceinline__ float min_image(float xj, float xi, float L, float in
 // is fetched two iterations ahead and its position one iteration ahead, so
 // the dependent index -> position gather overlaps the current pair's math.
 // Out-of-range slots re-use a valid index (loads stay in bounds).
+constexpr int kPrefetch = 8;
+
 struct NbrWalk {
   const int* __restrict__ list;
   const float4* __restrict__ pos;
@@ -87,6 +89,8 @@ struct NbrWalk {
     const float4 pj = p_ahead;
     p_ahead = pos[j_ahead];
     if (k + 2 < n) j_ahead = list[nbr_index(i, s + k + 2, cap)];
+    // pull the index row kPrefetch entries ahead into L1 (one 128-byte line per warp)
+    if (k + kPrefetch < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(list + nbr_index(i, s + k + kPrefetch, cap)));
     return pj;
   }
 };

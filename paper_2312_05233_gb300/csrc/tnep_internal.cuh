@@ -64,6 +64,7 @@ struct NbrArgs {
   StructGrid* grids;        // [S]
   StructBox* boxes;         // [S]
   int* struct_cells;        // [S+1] cells per structure, then exclusive scan
+  int* struct_flags;        // [S] bit 0: a coordinate lies outside [0, L) on a periodic axis
   int* atom_struct;         // [N] structure of each input atom
   int* atom_cell;           // [N]
   int* atom_slot;           // [N]

@@ -65,6 +65,11 @@ def test_neighbors_bitexact(tn, cell_div):
     frames, types, box = synth.water_small(3)
     structs = [synth.Structure(frames[f], types, box) for f in range(3)]
     rng = np.random.default_rng(3)
+    # unwrapped coordinates (shifted by whole box edges) take the per-pair rint path
+    unwrapped = (frames[0] + box * rng.integers(-1, 2, size=frames[0].shape)).astype(np.float32)
+    structs.append(synth.Structure(unwrapped, types, box))
+    big, bt_types, bbox = synth.water_grid_box(8, 24.84, rng)
+    structs.append(synth.Structure(np.mod(big, bbox).astype(np.float32), bt_types, bbox.astype(np.float32)))
     for n in (1, 7, 40):
         p, t, b = synth.water_cluster(n, rng)
         structs.append(synth.Structure(p.astype(np.float32), t, b.astype(np.float32)))
