@@ -339,3 +339,29 @@ def test_spectrum_parity(tn, kind, C):
     # device-resident series gives the same result
     f2, S2 = tn.tnep_spectrum(torch.from_numpy(series).cuda(), 0.5, kind, max_lag=250)
     assert np.array_equal(S2, S)
+
+
+def test_dense_cluster_large_lists(tn):
+    """~200 neighbours per atom: the lists regrow past the shared-memory
+    staging limit of the neighbour build, which then stages in global memory."""
+    rng = np.random.default_rng(41)
+    pts = []
+    while len(pts) < 200:
+        v = rng.uniform(-3.0, 3.0, 3)
+        if np.linalg.norm(v) < 3.0 and all(np.linalg.norm(v - q) >= 0.35 for q in pts):
+            pts.append(v)
+    pos = np.asarray(pts, np.float32)
+    types = rng.integers(0, 2, size=len(pts)).astype(np.int32)
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    cR, cA, lR, _ = tn.tnep_neighbors(ctx, [0, len(pts)], pos, None, cap_R=256, cap_A=256)
+    ref = oracle.neighbours_fp32(pos, np.zeros(3, np.float32), RC[0])
+    assert cR.min() == len(pts) - 1
+    for a in range(len(pts)):
+        assert np.array_equal(np.sort(lR[a, :cR[a]]), ref[a])
+    (mu, al), _ = tn.tnep_eval_batch(ctx, [0, len(pts)], pos, None, types)
+    for got, m in ((mu, om[0]), (al, om[1])):
+        r = oracle.evaluate(m, pos, None, types)
+        assert np.linalg.norm(got[0] - r.tensor) <= max(REL * np.linalg.norm(r.tensor),
+                                                        COND * np.abs(r.per_atom).sum())
+    ctx.close()
