@@ -257,10 +257,6 @@ __device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* 
   return n;
 }
 
-// Radial scratch lists up to this size (cap_R x 128 threads x 4 B) are staged
-// in shared memory.
-constexpr size_t kBuildStageMax = 100 * 1024;
-
 // Minimum-image difference with every operation rounded separately.
 __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
   float d = __fsub_rn(xj, xi);
@@ -269,14 +265,13 @@ __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL
 }
 
 // One thread per atom.  Radial entries go to a scratch list tagged with the
-// neighbour type (bits 29-31) -- a per-thread column of shared memory when
-// the capacity allows (SMEM), else global memory -- then the same thread
-// counting-sorts its own entries by type into the final radial list (stable:
-// ascending scan order inside each type) and records the per-type counts;
-// the radial moments kernel walks one type segment at a time.
-template <bool SMEM>
+// neighbour type (bits 29-31), then the same thread counting-sorts its own
+// entries by type into the final radial list (stable: ascending scan order
+// inside each type) and records the per-type counts; the radial moments
+// kernel walks one type segment at a time.  (Staging the scratch in shared
+// memory instead was measured slower: it limits the candidate scan to 12
+// warps per SM.)
 __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell, float rc2R, float rc2A) {
-  extern __shared__ int stage[];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_atoms) return;
   const float4 pi = a.pos4[i];
@@ -298,8 +293,8 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   const bool use_rint = nx < 0 || ny < 0 || nz < 0 || (a.struct_flags[s] & 1);
   nx = abs(nx); ny = abs(ny); nz = abs(nz);
   // scratch entry e of this thread lives at wR[e * ws]
-  int* wR = SMEM ? stage + threadIdx.x : a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
-  const int ws = SMEM ? (int)blockDim.x : 32;
+  int* wR = a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
+  constexpr int ws = 32;
   int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
   int cR = 0, cA = 0;
   for (int iz = 0; iz < nz; ++iz) {
@@ -401,14 +396,7 @@ cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st) {
     // sorted_cell reuses atom_slot (dead after the scatter)
     k_cell_sort<<<1216, 256, 0, st>>>(a, a.atom_slot);
     const float rc2R = a.rc_R * a.rc_R, rc2A = a.rc_A * a.rc_A;
-    const size_t stage_bytes = (size_t)a.cap_R * 128 * sizeof(int);
-    if (stage_bytes <= kBuildStageMax) {
-      cudaError_t e = cudaFuncSetAttribute(k_build<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_bytes);
-      if (e != cudaSuccess) return e;
-      k_build<true><<<(N + 127) / 128, 128, stage_bytes, st>>>(a, a.atom_slot, rc2R, rc2A);
-    } else {
-      k_build<false><<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
-    }
+    k_build<<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
   }
   return cudaGetLastError();
 }

@@ -342,8 +342,8 @@ def test_spectrum_parity(tn, kind, C):
 
 
 def test_dense_cluster_large_lists(tn):
-    """~200 neighbours per atom: the lists regrow past the shared-memory
-    staging limit of the neighbour build, which then stages in global memory."""
+    """~200 neighbours per atom: the neighbour lists regrow well past their
+    initial capacity (128 radial, 64 angular)."""
     rng = np.random.default_rng(41)
     pts = []
     while len(pts) < 200:
