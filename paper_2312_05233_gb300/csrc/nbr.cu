@@ -309,25 +309,45 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
         const float sx = xs[ix];
         const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
         ix = ie;
-        for (int j = j0; j < j1; ++j) {
-          const float4 pj = a.pos4[j];
-          float dx, dy, dz;
-          if (!use_rint) {
-            dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
-            dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
-            dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
-          } else {
-            dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
-            dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
-            dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
+        const bool noshift = !use_rint && sx == 0.0f && sy == 0.0f && sz == 0.0f;
+        // Test up to 32 candidates into acceptance bit masks, then append only
+        // the accepted ones (about one candidate in seven is accepted).
+        for (int jb = j0; jb < j1; jb += 32) {
+          const int je = min(jb + 32, j1);
+          unsigned mR = 0u, mA = 0u;
+          for (int j = jb; j < je; ++j) {
+            const float4 pj = a.pos4[j];
+            float dx, dy, dz;
+            if (noshift) {
+              dx = __fsub_rn(pj.x, pi.x);
+              dy = __fsub_rn(pj.y, pi.y);
+              dz = __fsub_rn(pj.z, pi.z);
+            } else if (!use_rint) {
+              dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
+              dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
+              dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
+            } else {
+              dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
+              dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
+              dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
+            }
+            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const unsigned bit = (j != i) ? (1u << (j - jb)) : 0u;
+            mR |= (r2 < rc2R) ? bit : 0u;
+            mA |= (r2 < rc2A) ? bit : 0u;
           }
-          const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-          const bool inR = (r2 < rc2R) && (j != i);
-          if (inR && cR < a.cap_R) wR[cR * ws] = j | (__float_as_int(pj.w) << kTypeShift);
-          cR += inR;
-          const bool inA = inR && (r2 < rc2A);
-          if (inA && cA < a.cap_A) wA[(size_t)cA * 32] = j;
-          cA += inA;
+          while (mR) {
+            const int j = jb + __ffs(mR) - 1;
+            mR &= mR - 1;
+            if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
+            ++cR;
+          }
+          while (mA) {
+            const int j = jb + __ffs(mA) - 1;
+            mA &= mA - 1;
+            if (cA < a.cap_A) wA[(size_t)cA * 32] = j;
+            ++cA;
+          }
         }
       }
     }
