@@ -315,8 +315,9 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
         for (int jb = j0; jb < j1; jb += 32) {
           const int je = min(jb + 32, j1);
           unsigned mR = 0u, mA = 0u;
+#pragma unroll 4
           for (int j = jb; j < je; ++j) {
-            const float4 pj = a.pos4[j];
+            const float4 pj = __ldg(&a.pos4[j]);
             float dx, dy, dz;
             if (noshift) {
               dx = __fsub_rn(pj.x, pi.x);
@@ -356,28 +357,43 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   a.cnt_A[i] = cA;
   if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
   if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
-  // counting sort of the radial entries by neighbour type
+  // counting sort of the radial entries by neighbour type; the scratch rows
+  // are read eight at a time so that eight loads are in flight per warp
   const int n = min(cR, a.cap_R);
   int cnt[kMaxTypes];
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u) cnt[u] = 0;
-  for (int e = 0; e < n; ++e) {
-    const int t = (unsigned)wR[e * ws] >> kTypeShift;
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    int v[8];
 #pragma unroll
-    for (int u = 0; u < kMaxTypes; ++u) cnt[u] += (t == u);
+    for (int q = 0; q < 8; ++q) v[q] = (e0 + q < n) ? wR[(size_t)(e0 + q) * ws] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int t = (e0 + q < n) ? (int)((unsigned)v[q] >> kTypeShift) : -1;
+#pragma unroll
+      for (int u = 0; u < kMaxTypes; ++u) cnt[u] += (t == u);
+    }
   }
   int off[kMaxTypes];
   int run = 0;
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u) { off[u] = run; run += cnt[u]; }
-  for (int e = 0; e < n; ++e) {
-    const int v = wR[e * ws];
-    const int t = (unsigned)v >> kTypeShift;
-    int dst = 0;
+  int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    int v[8];
 #pragma unroll
-    for (int u = 0; u < kMaxTypes; ++u)
-      if (t == u) { dst = off[u]; off[u] = dst + 1; }
-    a.nbr_R[nbr_index(i, dst, a.cap_R)] = v & kIndexMask;
+    for (int q = 0; q < 8; ++q) v[q] = (e0 + q < n) ? wR[(size_t)(e0 + q) * ws] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (e0 + q < n) {
+        const int t = (unsigned)v[q] >> kTypeShift;
+        int dst = 0;
+#pragma unroll
+        for (int u = 0; u < kMaxTypes; ++u)
+          if (t == u) { dst = off[u]; off[u] = dst + 1; }
+        outR[(size_t)dst * 32] = v[q] & kIndexMask;
+      }
+    }
   }
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u)
