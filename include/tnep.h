@@ -185,6 +185,41 @@ tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int 
                           int max_lag, int subtract_mean, double* freq_cm1, double* spec,
                           double* acf_out, void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of evaluation requests (one structure each).  Requests
+ * are copied in by tnep_submit and admitted while `max_slots` requests are
+ * not exceeded and the estimated device memory of the admitted, unfinished
+ * requests stays within `mem_budget_bytes` (else TNEP_ERR_BUSY; retry later).
+ * A worker thread keeps up to `n_pipelines` batches in flight, each on its
+ * own stream and resident workspace; a free pipeline takes every pending
+ * request (up to `max_batch_atoms` atoms) as one batch, so requests that
+ * arrive while others run are batched and overlap them on the device.  A
+ * structure's result is bitwise the same alone and in any batch.  While a
+ * server runs, the context must not be used by other calls.  Results are
+ * [n_models][C_m] float64 per request (models in context order). */
+typedef struct tnep_server tnep_server;
+typedef struct {
+  int n_atoms;
+  const float* pos;   /* [n_atoms][3] host memory */
+  const float* box;   /* [3] orthorhombic edges (0 = open axis) or NULL = open */
+  const int* types;   /* [n_atoms] host memory */
+} tnep_request;
+
+tnep_status tnep_server_start(tnep_ctx* ctx, size_t mem_budget_bytes, int max_slots, int n_pipelines,
+                              int max_batch_atoms, tnep_server** out);
+/* Copies the request; TNEP_ERR_BUSY when it cannot be admitted now. */
+tnep_status tnep_submit(tnep_server* server, const tnep_request* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 and the result in `out` once finished (the ticket is then released);
+ * latency_s (may be NULL) = submission to completion, in seconds. */
+tnep_status tnep_poll(tnep_server* server, uint64_t ticket, double* out, int* done, double* latency_s);
+/* Blocks up to timeout_s seconds; TNEP_ERR_TIMEOUT if the request is not finished by then. */
+tnep_status tnep_wait(tnep_server* server, uint64_t ticket, double* out, double timeout_s, double* latency_s);
+/* stats[6]: completed requests, batches launched, atoms evaluated, admitted bytes in use,
+ * requests in flight, requests pending. */
+tnep_status tnep_server_stats(tnep_server* server, double stats[6]);
+/* Finishes admitted requests (bounded by their device work), then frees the server. */
+void tnep_server_stop(tnep_server* server);
+
 /* Longest series tnep_spectrum_noalloc accepts (its scratch is sized for it). */
 #define TNEP_NOALLOC_MAX_T 32768
 

@@ -1,0 +1,190 @@
+// Host-side engine of libtnep: device workspaces, the batch pipeline and
+// error reporting.  Shared by the C entry points (api.cu) and the serving
+// loop (serve.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "tnep_internal.cuh"
+
+namespace tnep {
+
+tnep_status fail(tnep_status s, const std::string& msg);
+const char* last_error_cstr();
+tnep_status cuda_fail(cudaError_t e, const char* what);
+
+#define TNEP_CUDA(expr)                                     \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::tnep::cuda_fail(_e, #expr); \
+  } while (0)
+
+#define TNEP_TRY(expr)                    \
+  do {                                    \
+    tnep_status _s = (expr);              \
+    if (_s != TNEP_OK) return _s;         \
+  } while (0)
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t m) {
+    if (m <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    const size_t want = std::max<size_t>(std::max<size_t>(m, 1), m + m / 4);
+    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    n = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+template <class T>
+struct PinBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t m) {
+    if (m <= n && p) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    const size_t want = std::max<size_t>(m, 1);
+    cudaError_t e = cudaHostAlloc((void**)&p, want * sizeof(T), cudaHostAllocDefault);
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    n = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct Model {
+  tnep_model_desc d{};
+  int nR = 0, nA = 0, bR = 0, bA = 0, D = 0, nets = 0, variant = -1, C = 0;
+  ModelLayout lay{};
+  std::vector<float> params;
+  std::vector<float> scaler;
+  float* d_packed = nullptr;
+};
+
+// Device workspace of one in-flight batch.
+struct Workspace {
+  DevBuf<int> offsets, atom_struct, atom_cell, atom_slot, cell_count, cell_start, cell_atoms;
+  DevBuf<int> sorted_orig, orig_sorted, sorted_struct, struct_cells, cnt_R, cnt_A, nbr_R, nbr_A;
+  DevBuf<int> nbr_tmp, seg_R, struct_flags;
+  DevBuf<float> mom;        // radial moments [slots][atom_stride]
+  int mom_v0 = -1, mom_w0 = -1;
+  DevBuf<float4> pos4;
+  DevBuf<StructGrid> grids;
+  DevBuf<StructBox> boxes;
+  DevBuf<float> per_atom;   // [model][pop][C][atom_stride]
+  DevBuf<double> out;       // [model][S][C]
+  DevBuf<double> partial;   // reduction partials
+  int max_atoms = 0;        // largest structure of the batch
+  DevBuf<float> pos_stage[2], box_stage;
+  DevBuf<int> types_stage;
+  DevStatus* d_status = nullptr;  // device status word of this workspace
+  PinBuf<DevStatus> h_status;     // pinned host copy
+  int atom_stride = 0;
+  int cells_cap = 0;
+  int cap_R = 0, cap_A = 0;  // caps the lists were built with
+  void release() {
+    for (auto* b : {&offsets, &atom_struct, &atom_cell, &atom_slot, &cell_count, &cell_start, &cell_atoms,
+                    &sorted_orig, &orig_sorted, &sorted_struct, &struct_cells, &cnt_R, &cnt_A, &nbr_R, &nbr_A,
+                    &types_stage, &nbr_tmp, &seg_R, &struct_flags})
+      b->release();
+    pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release(); partial.release();
+    mom.release();
+    pos_stage[0].release(); pos_stage[1].release(); box_stage.release();
+    if (d_status) cudaFree(d_status);
+    d_status = nullptr;
+    h_status.release();
+  }
+};
+
+bool is_device_ptr(const void* p);
+int round_up(int x, int m);
+
+}  // namespace tnep
+
+struct tnep_ctx {
+  using Workspace = tnep::Workspace;
+  using Model = tnep::Model;
+  template <class T> using PinBuf = tnep::PinBuf<T>;
+  template <class T> using DevBuf = tnep::DevBuf<T>;
+  int device = 0;
+  cudaStream_t stream = nullptr, copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_consumed[2] = {nullptr, nullptr};
+  cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
+  std::vector<cudaEvent_t> ev_pass;  // 3 timing events per pass, created on demand
+  int n_types = 0;
+  float rc_R = 0.f, rc_A = 0.f;
+  std::vector<Model> models;
+  std::vector<std::string> type_names;
+  Workspace ws;
+  PinBuf<double> h_out;
+  PinBuf<float> h_stage_f;
+  PinBuf<int> h_stage_i;
+  DevBuf<float> pop_params;
+  DevBuf<double> pop_target, pop_rmse;
+  int cap_R = 128, cap_A = 64;
+  int max_neighbors = 1024;
+  int frames_per_batch = 0;
+  int cell_div = 1;
+  double last_kernel_ms = 0.0;
+  double last_nbr_ms = 0.0;
+  int last_launches = 0;
+};
+
+
+namespace tnep {
+
+tnep_status pack_model(tnep_ctx* c, Model& m);
+void pack_params(const Model& m, int T, const float* flat, const float* scaler, float* out);
+size_t expected_params(const tnep_model_desc& d, int T);
+tnep_status validate_model(const tnep_model_desc& d, int T);
+tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const int* h_offsets, const float* d_pos,
+                        const float* d_box, const int* d_types, int types_period);
+tnep_status compute_moments(tnep_ctx* c, Workspace& w, cudaStream_t st, int N, bool need_v, bool need_w);
+bool any_rank(const tnep_ctx* c, int rank);
+FusedArgs fused_args(tnep_ctx* c, Workspace& w, const Model& m, int N);
+int total_C(const tnep_ctx* c);
+tnep_status pass_events(tnep_ctx* c, int b, cudaEvent_t** ev);
+tnep_status sum_pass_times(tnep_ctx* c, int n_pass);
+tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done);
+tnep_status check_status(tnep_ctx* c, const DevStatus& s, bool* regrow);
+tnep_status reset_status(Workspace& w, cudaStream_t st);
+tnep_status finish(tnep_ctx* c, Workspace& w, cudaStream_t st, bool* regrow);
+tnep_status copy_out_bytes(void* dst, const void* src, size_t bytes, cudaStream_t st);
+template <class T>
+tnep_status copy_out(T* dst, const T* src, size_t count, cudaStream_t st) {
+  return copy_out_bytes(dst, src, sizeof(T) * count, st);
+}
+template <class T>
+tnep_status stage_in(const T* src, size_t n, DevBuf<T>& buf, const T** dev, cudaStream_t st) {
+  if (!src || n == 0) { *dev = src; return TNEP_OK; }
+  if (is_device_ptr(src)) { *dev = src; return TNEP_OK; }
+  TNEP_CUDA(buf.ensure(n));
+  TNEP_CUDA(cudaMemcpyAsync(buf.p, src, sizeof(T) * n, cudaMemcpyHostToDevice, st));
+  *dev = buf.p;
+  return TNEP_OK;
+}
+cudaStream_t pick_stream(tnep_ctx* c, void* stream);
+int default_frames_per_batch(int n_atoms, int n_frames);
+
+}  // namespace tnep

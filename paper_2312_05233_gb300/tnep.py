@@ -35,6 +35,7 @@ EXPORTED = [
     "tnep_create", "tnep_destroy", "tnep_last_error", "tnep_output_dim", "tnep_eval",
     "tnep_eval_batch", "tnep_neighbors", "tnep_eval_population", "tnep_spectrum",
     "tnep_set_option", "tnep_get_option", "tnep_spectrum_noalloc",
+    "tnep_server_start", "tnep_submit", "tnep_poll", "tnep_wait", "tnep_server_stats", "tnep_server_stop",
 ]
 TNEP_NOALLOC_MAX_T = 32768
 
@@ -43,6 +44,10 @@ class TnepError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class Request(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("pos", C.c_void_p), ("box", C.c_void_p), ("types", C.c_void_p)]
 
 
 class ModelDesc(C.Structure):
@@ -72,6 +77,12 @@ def _load():
         "tnep_spectrum": (C.c_int, [dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, vp]),
         "tnep_spectrum_noalloc": (C.c_int, [dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp,
                                             dp, vp]),
+        "tnep_server_start": (C.c_int, [vp, C.c_size_t, C.c_int, C.c_int, C.c_int, C.POINTER(vp)]),
+        "tnep_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "tnep_poll": (C.c_int, [vp, C.c_uint64, dp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "tnep_wait": (C.c_int, [vp, C.c_uint64, dp, C.c_double, C.POINTER(C.c_double)]),
+        "tnep_server_stats": (C.c_int, [vp, dp]),
+        "tnep_server_stop": (None, [vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -356,3 +367,70 @@ def tnep_spectrum_noalloc(series, dt_fs: float, kind: int, freq_out, spec_out, a
     Tn, Cn = int(series.shape[0]), int(series.shape[1])
     _check(_lib.tnep_spectrum_noalloc(S.ptr, Tn, Cn, float(dt_fs), int(kind), int(max_lag),
                                       int(bool(subtract_mean)), F.ptr, P.ptr, A.ptr, _stream_ptr(stream)))
+
+
+TNEP_ERR_BUSY = 8
+TNEP_ERR_TIMEOUT = 6
+
+
+class Server:
+    """Owns a tnep_server handle (continuous-batching serving loop)."""
+
+    def __init__(self, handle, ctx):
+        self.handle = handle
+        self.ctx = ctx
+        self.width = sum(ctx.dims)
+
+    def submit(self, pos, types, box=None):
+        """Returns a ticket, or None when the request is not admitted (BUSY)."""
+        p = np.ascontiguousarray(pos, dtype=np.float32)
+        t = np.ascontiguousarray(types, dtype=np.int32)
+        b = None if box is None else np.ascontiguousarray(box, dtype=np.float32)
+        req = Request(len(t), p.ctypes.data if p.size else None, b.ctypes.data if b is not None else None,
+                      t.ctypes.data if t.size else None)
+        tk = C.c_uint64()
+        st = _lib.tnep_submit(self.handle, C.byref(req), C.byref(tk))
+        if st == TNEP_ERR_BUSY:
+            return None
+        _check(st)
+        return tk.value
+
+    def poll(self, ticket):
+        """(done, result [width] or None, latency_s)."""
+        out = np.zeros(self.width)
+        done = C.c_int()
+        lat = C.c_double()
+        _check(_lib.tnep_poll(self.handle, C.c_uint64(ticket), out.ctypes.data, C.byref(done), C.byref(lat)))
+        return (bool(done.value), out if done.value else None, lat.value)
+
+    def wait(self, ticket, timeout_s=60.0):
+        """(result [width], latency_s); raises TnepError(TIMEOUT) when not finished in time."""
+        out = np.zeros(self.width)
+        lat = C.c_double()
+        _check(_lib.tnep_wait(self.handle, C.c_uint64(ticket), out.ctypes.data, float(timeout_s), C.byref(lat)))
+        return out, lat.value
+
+    def stats(self):
+        st = np.zeros(6)
+        _check(_lib.tnep_server_stats(self.handle, st.ctypes.data))
+        return dict(completed=st[0], batches=st[1], atoms=st[2], bytes_in_use=st[3], inflight=st[4],
+                    pending=st[5])
+
+    def stop(self):
+        if self.handle:
+            _lib.tnep_server_stop(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
+
+
+def tnep_server_start(ctx: Context, mem_budget_bytes: int = 8 << 30, max_slots: int = 4096, n_pipelines: int = 3,
+                      max_batch_atoms: int = 1 << 19) -> Server:
+    h = C.c_void_p()
+    _check(_lib.tnep_server_start(ctx.handle, int(mem_budget_bytes), int(max_slots), int(n_pipelines),
+                                  int(max_batch_atoms), C.byref(h)))
+    return Server(h, ctx)

@@ -32,7 +32,7 @@ HOH_ANGLE_DEG = 104.5
 
 __all__ = [
     "SEED_BASE", "seed_for", "HyperParams", "n_params", "model_params",
-    "default_q_scaler", "random_rotation", "water_molecule_frame",
+    "default_q_scaler", "random_rotation", "random_rotations", "water_molecule_frame",
     "water_box", "water_grid_box", "jitter_frames", "random_walk_frames",
     "bzo_supercell", "thermal_frames", "water_cluster", "anion",
     "poisson_arrivals", "Structure", "StructureBatch", "concat_structures",
@@ -119,12 +119,22 @@ def water_molecule_frame() -> np.ndarray:
     ])
 
 
+def random_rotations(n: int, rng: np.random.Generator) -> np.ndarray:
+    """n uniform random rotations [n,3,3] from normalised Gaussian quaternions."""
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1)[:, None]
+    w, x, y, z = q.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)], -1),
+        np.stack([2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)], -1),
+        np.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], -1),
+    ], 1)
+
+
 def _place_waters(centres: np.ndarray, rng: np.random.Generator) -> np.ndarray:
     mol = water_molecule_frame()
-    out = np.empty((len(centres) * 3, 3))
-    for m, c in enumerate(centres):
-        out[3 * m:3 * m + 3] = c + mol @ random_rotation(rng).T
-    return out
+    R = random_rotations(len(centres), rng)
+    return (centres[:, None, :] + np.einsum("ka,mba->mkb", mol, R)).reshape(-1, 3)
 
 
 def water_grid_box(n_side: int, L: float, rng: np.random.Generator):
