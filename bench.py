@@ -127,6 +127,72 @@ def oracle_sample(hps, params, frame, box, types, n_centers, seed=0):
     return dt, torch.get_num_threads()
 
 
+def serving_bench(tn, synth, device, rates, n_req):
+    """Poisson arrivals of mixed requests (open anions, periodic water) served
+    by the continuous-batching server vs the plain per-request path."""
+    import threading
+    rng = np.random.default_rng(synth.seed_for(5))
+    reqs = synth.serving_requests(n_req, rng)
+    atoms = np.array([len(r.types) for r in reqs])
+    hp = synth.HyperParams(n_types=6, rank=1)
+    model = tn.Model.from_hyper(hp, synth.model_params(hp, rng), synth.default_q_scaler(hp))
+    ctx = tn.tnep_create([model], 6, RC, device=device)
+    for r in reqs[:8]:  # warm-up of both paths
+        tn.tnep_eval_batch(ctx, [0, len(r.types)], r.pos, r.box[None], r.types)
+    out = []
+    for rate in rates:
+        arr = synth.poisson_arrivals(rate, n_req, np.random.default_rng(synth.seed_for(5, int(rate))))
+        # served
+        srv = tn.tnep_server_start(ctx, mem_budget_bytes=16 << 30, max_slots=4096, n_pipelines=3,
+                                   max_batch_atoms=1 << 19)
+        for r in reqs[:8]:
+            srv.wait(srv.submit(r.pos, r.types, r.box))
+        tickets = [None] * n_req
+        done = np.zeros(n_req)
+        t0 = time.perf_counter()
+
+        def waiter():
+            for i in range(n_req):
+                while tickets[i] is None:
+                    time.sleep(2e-5)
+                srv.wait(tickets[i], timeout_s=120.0)
+                done[i] = time.perf_counter()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        for i, r in enumerate(reqs):
+            while time.perf_counter() < t0 + arr[i]:
+                pass
+            tk = srv.submit(r.pos, r.types, r.box)
+            while tk is None:
+                time.sleep(5e-5)
+                tk = srv.submit(r.pos, r.types, r.box)
+            tickets[i] = tk
+        th.join()
+        st = srv.stats()
+        srv.stop()
+        lat_s = done - (t0 + arr)
+        served = {"atom_frames_per_s": float(atoms.sum() / (done.max() - t0)),
+                  "p50_ms": float(np.percentile(lat_s, 50) * 1e3), "p99_ms": float(np.percentile(lat_s, 99) * 1e3),
+                  "batches": int(st["batches"])}
+        # plain: one tnep_eval_batch per request, first come first served
+        done_p = np.zeros(n_req)
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            while time.perf_counter() < t0 + arr[i]:
+                pass
+            tn.tnep_eval_batch(ctx, [0, len(r.types)], r.pos, r.box[None], r.types)
+            done_p[i] = time.perf_counter()
+        lat_p = done_p - (t0 + arr)
+        plain = {"atom_frames_per_s": float(atoms.sum() / (done_p.max() - t0)),
+                 "p50_ms": float(np.percentile(lat_p, 50) * 1e3), "p99_ms": float(np.percentile(lat_p, 99) * 1e3)}
+        out.append({"rate_per_s": rate, "served": served, "plain": plain})
+    ctx.close()
+    return {"workload": f"{n_req} requests per rate, 50/50 open anions (20-60 atoms, 6 types) and periodic "
+                        f"water (192-24,000 atoms), rank-1 model, Poisson arrivals; latency from arrival",
+            "mean_atoms": float(atoms.mean()), "rates": out}
+
+
 def run_reference(args, rank, world):
     """FP64 CPU oracle arm: bounded samples of the same workload."""
     import synth
@@ -166,6 +232,9 @@ def main():
     ap.add_argument("--ref-centers", type=int, default=400)
     ap.add_argument("--cpu-centers", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rates", default="300,3000")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -296,6 +365,9 @@ def main():
                      "fused_launches_per_step": fused_launches / args.steps},
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_serve:
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        line["served"] = serving_bench(tn, synth, local, rates, args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, cores = oracle_sample(hps, params, frames[0], box, types, args.cpu_centers)
         line["cpu_baseline"] = {"value": args.cpu_centers / dt, "unit": "atom-frames/s", "cores": cores,
