@@ -202,6 +202,28 @@ def serving_bench(tn, synth, device, rates, n_req):
             "mean_atoms": float(atoms.mean()), "rates": out}
 
 
+# ------------------------------------------------------------------ multi-rank
+def shard_seed_k(rank: int) -> int:
+    """Each rank evaluates its own trajectory (weak scaling over frames):
+    rank r draws the bulk-water random walk with seed offset r."""
+    return int(rank)
+
+
+def max_over_ranks(dist, x: float, device, world: int) -> float:
+    """The slowest rank's time (the job's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_units(frames: int, atoms: int, world: int) -> int:
+    """Atom-frames processed by the whole job per step."""
+    return int(frames) * int(atoms) * int(world)
+
+
 def run_reference(args, rank, world):
     """FP64 CPU oracle arm: bounded samples of the same workload."""
     import synth
@@ -267,10 +289,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    # each rank evaluates its own trajectory shard (weak scaling over frames)
-    frames, types, box = synth.water_bulk(n_frames=args.frames)
-    if rank:
-        frames = frames[::-1].copy()
+    # each rank evaluates its own trajectory (weak scaling over frames)
+    frames, types, box = synth.water_bulk(n_frames=args.frames, seed_k=shard_seed_k(rank))
     F, N = frames.shape[0], frames.shape[1]
     models, hps, params = make_models(tn, synth)
     ctx = tn.tnep_create(models, 2, RC, device=local)
@@ -309,13 +329,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     for _ in range(args.warmup):
         step_device()
     barrier()
@@ -333,7 +346,7 @@ def main():
         ev1.record(stream)
         barrier()
     launches = tn.tnep_get_option(ctx, tn.TNEP_OPT_KERNEL_LAUNCHES_TOTAL) - l0
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1) / args.steps, dev, world)
 
     # end to end through the public API with pinned host buffers
     for _ in range(1):
@@ -343,7 +356,7 @@ def main():
     for _ in range(args.steps):
         step_e2e()
     barrier()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+    e2e_ms = max_over_ranks(dist, (time.perf_counter() - t0) * 1e3 / args.steps, dev, world)
 
     # neighbour statistics of the last frame for the flop model
     offs = np.array([0, N])
@@ -355,7 +368,7 @@ def main():
     clocks = clk.summary()
     peak_tflops = SMS * FP32_LANES * 2 * 2070e6 / 1e12
 
-    units = F * N * world
+    units = job_units(F, N, world)
     value = units / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "atom-frames/s", "n_gpus": world, "steps": args.steps,

@@ -283,9 +283,9 @@ def water_small(n_frames: int = 100):
     return frames, types, box.astype(np.float32)
 
 
-def water_bulk(n_frames: int = 2000, n_side: int = 24, L: float = 74.5, sigma: float = 0.01):
+def water_bulk(n_frames: int = 2000, n_side: int = 24, L: float = 74.5, sigma: float = 0.01, seed_k: int = 0):
     """13,824 H2O (41,472 atoms) in a 74.5 A cube, random walk 0.01 A/step."""
-    rng = np.random.default_rng(seed_for(2))
+    rng = np.random.default_rng(seed_for(2, seed_k))
     base, types, box = water_grid_box(n_side, L, rng)
     frames = random_walk_frames(base, box, n_frames, sigma, rng)
     return frames, types, box.astype(np.float32)
