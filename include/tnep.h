@@ -166,6 +166,30 @@ tnep_status tnep_eval_population(tnep_ctx* ctx, int model, int n_pop, const floa
                                  const float* box, const int* types, const double* target,
                                  double* rmse, double* out, void* stream);
 
+/* Training-style population evaluation with resident structures (Sec. II.D:
+ * the evolution strategy evaluates a population on the training set every
+ * generation).  tnep_population_create builds the neighbour lists and radial
+ * moments of the structures once (they do not depend on the parameters),
+ * times the candidate launch shapes of the fused kernel (64 or 128 atoms per
+ * CTA; atom-block-major or individual-major CTA order) on these structures
+ * and keeps the fastest, and captures one generation -- parameter upload,
+ * one fused launch over all n_pop x atoms, FP64 reduction, RMSE, read-back --
+ * in a CUDA graph.  `params` [n_pop][n_params] (host) is used for the timing.
+ * Arguments otherwise as tnep_eval_population. */
+typedef struct tnep_population tnep_population;
+tnep_status tnep_population_create(tnep_ctx* ctx, int model, int n_pop, const float* params, int n_structs,
+                                   const int* atom_offsets, const float* pos, const float* box,
+                                   const int* types, const double* target, tnep_population** out);
+/* Replays the captured generation for new parameters [n_pop][n_params] (host):
+ * rmse [n_pop], out NULL or [n_pop][n_structs][C] (host).  Synchronous. */
+tnep_status tnep_population_eval(tnep_population* pop, const float* params, double* rmse, double* out);
+/* info[8]: atoms per CTA and CTA order chosen, the four timed candidates (ms per
+ * generation: 128/atom-major, 128/individual-major, 64/atom-major,
+ * 64/individual-major; -1 = not applicable), last generation's device time (ms),
+ * atoms in the structure set. */
+tnep_status tnep_population_info(const tnep_population* pop, double info[8]);
+void tnep_population_destroy(tnep_population* pop);
+
 /* Spectrum kinds for tnep_spectrum. */
 enum {
   TNEP_SPECTRUM_IR = 0,          /* series [T][3] = mu(t); omega^2 * lineshape (Eq. 6) */
@@ -249,7 +273,7 @@ tnep_status tnep_spectrum_noalloc(const double* series, int T, int C, double dt_
 enum {
   TNEP_OPT_FRAMES_PER_BATCH = 0,    /* frames per device pass in tnep_eval (0 = automatic) */
   TNEP_OPT_MAX_NEIGHBORS = 1,       /* hard cap on neighbours per atom (default 1024); lists grow up to it */
-  TNEP_OPT_BLOCK_ATOMS = 2,         /* read-only: atoms per CTA of the fused kernel (128) */
+  TNEP_OPT_BLOCK_ATOMS = 2,         /* atoms per CTA of the fused kernel: 64 or 128 (default 128) */
   TNEP_OPT_LAST_KERNEL_MS = 3,      /* read-only: device time of the tensor kernels (radial moments + fused) of the last call (ms) */
   TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2} (default 1) */
   TNEP_OPT_LAST_KERNEL_LAUNCHES = 5,/* read-only: fused-kernel launches in the last call */

@@ -91,7 +91,7 @@ tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types
       e = cudaMemcpy(m.d_packed, packed.data(), sizeof(float) * m.lay.words, cudaMemcpyHostToDevice);
     c->models.push_back(std::move(m));
     if (e != cudaSuccess) return bail(cuda_fail(e, "model upload"));
-    if (fused_smem_bytes(c->models.back().variant, c->models.back().lay) > 227 * 1024)
+    if (fused_smem_bytes(c->models.back().variant, c->models.back().lay, kFusedBlockMax) > 227 * 1024)
       return bail(fail(TNEP_ERR_UNSUPPORTED, "model too large for shared memory"));
   }
   *out = c;
@@ -141,7 +141,8 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       c->max_neighbors = (int)value;
       return TNEP_OK;
     case TNEP_OPT_BLOCK_ATOMS:
-      if (value != kFusedBlock) return fail(TNEP_ERR_UNSUPPORTED, "this build uses 128 atoms per CTA");
+      if (value != 64 && value != 128) return fail(TNEP_ERR_INVALID, "atoms per CTA must be 64 or 128");
+      c->block_atoms = (int)value;
       return TNEP_OK;
     case TNEP_OPT_CELL_DIV:
       if (value != 1 && value != 2) return fail(TNEP_ERR_INVALID, "cell subdivision must be 1 or 2");
@@ -157,7 +158,7 @@ tnep_status tnep_get_option(const tnep_ctx* c, int option, double* value) {
   switch (option) {
     case TNEP_OPT_FRAMES_PER_BATCH: *value = c->frames_per_batch; return TNEP_OK;
     case TNEP_OPT_MAX_NEIGHBORS: *value = c->max_neighbors; return TNEP_OK;
-    case TNEP_OPT_BLOCK_ATOMS: *value = kFusedBlock; return TNEP_OK;
+    case TNEP_OPT_BLOCK_ATOMS: *value = c->block_atoms; return TNEP_OK;
     case TNEP_OPT_LAST_KERNEL_MS: *value = c->last_kernel_ms; return TNEP_OK;
     case TNEP_OPT_CELL_DIV: *value = c->cell_div; return TNEP_OK;
     case TNEP_OPT_LAST_KERNEL_LAUNCHES: *value = c->last_launches; return TNEP_OK;
@@ -420,7 +421,7 @@ tnep_status tnep_eval_population(tnep_ctx* c, int model, int n_pop, const float*
     f.per_atom_stride = pa_pop;
     cudaEvent_t* ev = nullptr;
     TNEP_TRY(pass_events(c, 0, &ev));
-    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, n_pop, st));
+    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, n_pop, c->block_atoms, st));
     TNEP_CUDA(cudaEventRecord(ev[2], st));
     TNEP_CUDA(w.partial.ensure((size_t)n_pop * n_structs * reduce_chunks(w.max_atoms) * m.C));
     TNEP_CUDA(launch_reduce(n_structs, n_pop, w.offsets.p, w.max_atoms, w.per_atom.p, pa_pop, w.atom_stride, m.C,

@@ -289,7 +289,7 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
     FusedArgs f = fused_args(c, w, m, N);
     f.per_atom = w.per_atom.p + k * per_model;
     f.per_atom_stride = 0;
-    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, st));
+    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, st));
   }
   if (ev_done) TNEP_CUDA(cudaEventRecord(ev_done, st));
   TNEP_CUDA(w.partial.ensure((size_t)std::max(S, 1) * reduce_chunks(w.max_atoms) * 9));

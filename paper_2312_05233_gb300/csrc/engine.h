@@ -146,6 +146,7 @@ struct tnep_ctx {
   int max_neighbors = 1024;
   int frames_per_batch = 0;
   int cell_div = 1;
+  int block_atoms = 128;  // atoms per CTA of the fused kernel (64 or 128)
   double last_kernel_ms = 0.0;
   double last_nbr_ms = 0.0;
   int last_launches = 0;

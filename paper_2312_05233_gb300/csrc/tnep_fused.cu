@@ -184,8 +184,8 @@ __device__ __forceinline__ float trace_m3(const float* a, float* grad) {
   return tr;
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK>
-__global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant__ FusedArgs a) {
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK>
+__global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant__ FusedArgs a) {
   constexpr int NLM = LMAX * (LMAX + 2);
   constexpr int D = NR + NA * LMAX + (FB ? NA : 0);
   constexpr int DP = (D + 3) & ~3;
@@ -195,15 +195,18 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
   extern __shared__ float4 sm4[];
   float* sm = reinterpret_cast<float*>(sm4);
   const ModelLayout& Ly = a.lay;
-  const int pop = blockIdx.y;
+  // CTA -> (atom block, individual); with pop_major the individual varies
+  // fastest so that CTAs running together share an atom block's lists.
+  const int pop = a.pop_major ? blockIdx.x : blockIdx.y;
+  const int ablk = a.pop_major ? blockIdx.y : blockIdx.x;
   {
     const float4* src = reinterpret_cast<const float4*>(a.model + (size_t)pop * a.model_stride);
     for (int k = threadIdx.x; k < (Ly.words >> 2); k += blockDim.x) sm4[k] = src[k];
   }
   __syncthreads();
   const int tid = threadIdx.x;
-  float* scratch = sm + Ly.words + tid;  // slot s at scratch[s * kFusedBlock]
-  const int i = blockIdx.x * kFusedBlock + tid;
+  float* scratch = sm + Ly.words + tid;  // slot s at scratch[s * BLK]
+  const int i = ablk * BLK + tid;
   if (i >= a.n_atoms) return;
 
   const float4 pi = a.pos4[i];
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
       for (int lm = 0; lm < NLM; ++lm) {
         const float v = A[n * NLM + lm];
         q[NR + (l_of(lm) - 1) * NA + n] += wlm(lm) * v * v;
-        scratch[(n * NLM + lm) * kFusedBlock] = v;
+        scratch[(n * NLM + lm) * BLK] = v;
       }
       if constexpr (FB) {
         float gr[5];
@@ -357,11 +360,11 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
     for (int n = 0; n < NA; ++n) {
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm)
-        G[n * NLM + lm] = 2.f * wlm(lm) * e[NR + (l_of(lm) - 1) * NA + n] * scratch[(n * NLM + lm) * kFusedBlock];
+        G[n * NLM + lm] = 2.f * wlm(lm) * e[NR + (l_of(lm) - 1) * NA + n] * scratch[(n * NLM + lm) * BLK];
       if constexpr (FB) {
         float a2[5], gr[5];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) a2[m] = scratch[(n * NLM + 3 + m) * kFusedBlock];
+        for (int m = 0; m < 5; ++m) a2[m] = scratch[(n * NLM + 3 + m) * BLK];
         trace_m3(a2, gr);
         const float e4 = kC4 * e[NR + LMAX * NA + n];
 #pragma unroll
@@ -425,21 +428,22 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(const __grid_constant_
   for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB>
-cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
-  const dim3 grid((a.n_atoms + kFusedBlock - 1) / kFusedBlock, n_pop);
-  if (rank == 1) {
-    auto fn = k_fused<NR, NA, BR, BA, LMAX, FB, 1>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, kFusedBlock, smem, st>>>(a);
-  } else {
-    auto fn = k_fused<NR, NA, BR, BA, LMAX, FB, 2>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, kFusedBlock, smem, st>>>(a);
-  }
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK>
+cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
+  const int nblk = (a.n_atoms + BLK - 1) / BLK;
+  if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
+  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK> : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, BLK, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB>
+cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, size_t smem, cudaStream_t st) {
+  if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64>(rank, a, n_pop, smem, st);
+  return launch_block<NR, NA, BR, BA, LMAX, FB, 128>(rank, a, n_pop, smem, st);
 }
 
 // Per-structure FP64 sums in two deterministic stages: CTA (s, chunk) sums a
@@ -526,20 +530,21 @@ int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb) {
   return -1;
 }
 
-size_t fused_smem_bytes(int variant, const ModelLayout& lay) {
+size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block) {
   int slots = 0;
   if (variant == kVarStd) slots = 5 * 24;
   if (variant == kVarSmall) slots = 3 * 15;
-  return (size_t)(lay.words + slots * kFusedBlock) * sizeof(float);
+  return (size_t)(lay.words + slots * block) * sizeof(float);
 }
 
-cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, cudaStream_t st) {
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, cudaStream_t st) {
   if (a.n_atoms <= 0 || n_pop <= 0) return cudaSuccess;
+  if (block != 64 && block != 128) return cudaErrorInvalidValue;
   count_launches(1);
-  const size_t smem = fused_smem_bytes(variant, a.lay);
+  const size_t smem = fused_smem_bytes(variant, a.lay, block);
   switch (variant) {
-    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, smem, st);
-    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, smem, st);
+    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, block, smem, st);
+    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, block, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -9,7 +9,7 @@
 namespace tnep {
 
 constexpr int kMaxTypes = 8;
-constexpr int kFusedBlock = 128;  // atoms per CTA of the fused kernel (one atom per thread)
+constexpr int kFusedBlockMax = 128;  // atoms per CTA of the fused kernel (one atom per thread): 64 or 128
 // Radial scratch entries carry the neighbour type in bits 29-31, so a batch
 // holds fewer than 2^29 atoms.
 constexpr int kTypeShift = 29;
@@ -137,14 +137,15 @@ struct FusedArgs {
   float* per_atom;           // [pop][C][atom_stride] (SoA, sorted order)
   size_t per_atom_stride;    // floats between individuals
   int atom_stride;           // row stride of the SoA output
+  int pop_major;             // 1: blockIdx.x = individual, blockIdx.y = atom block
 };
 
 // Kernel variant keys (must match the compiled instantiations).
 enum Variant { kVarStd = 0, kVarSmall = 1, kVarCount = 2 };
 
 int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb);
-size_t fused_smem_bytes(int variant, const ModelLayout& lay);
-cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, cudaStream_t st);
+size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block);
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, cudaStream_t st);
 
 // Per-structure FP64 reduction of per-atom contributions.  `max_atoms` is
 // the largest structure; `partial` holds n_pop * n_structs * reduce_chunks(max_atoms) * C doubles.

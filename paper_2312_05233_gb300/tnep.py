@@ -36,6 +36,7 @@ EXPORTED = [
     "tnep_eval_batch", "tnep_neighbors", "tnep_eval_population", "tnep_spectrum",
     "tnep_set_option", "tnep_get_option", "tnep_spectrum_noalloc",
     "tnep_server_start", "tnep_submit", "tnep_poll", "tnep_wait", "tnep_server_stats", "tnep_server_stop",
+    "tnep_population_create", "tnep_population_eval", "tnep_population_info", "tnep_population_destroy",
 ]
 TNEP_NOALLOC_MAX_T = 32768
 
@@ -83,6 +84,10 @@ def _load():
         "tnep_wait": (C.c_int, [vp, C.c_uint64, dp, C.c_double, C.POINTER(C.c_double)]),
         "tnep_server_stats": (C.c_int, [vp, dp]),
         "tnep_server_stop": (None, [vp]),
+        "tnep_population_create": (C.c_int, [vp, C.c_int, C.c_int, fp, C.c_int, ip, fp, fp, vp, dp, C.POINTER(vp)]),
+        "tnep_population_eval": (C.c_int, [vp, fp, dp, dp]),
+        "tnep_population_info": (C.c_int, [vp, dp]),
+        "tnep_population_destroy": (None, [vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -434,3 +439,51 @@ def tnep_server_start(ctx: Context, mem_budget_bytes: int = 8 << 30, max_slots: 
     _check(_lib.tnep_server_start(ctx.handle, int(mem_budget_bytes), int(max_slots), int(n_pipelines),
                                   int(max_batch_atoms), C.byref(h)))
     return Server(h, ctx)
+
+
+class Population:
+    """Owns a tnep_population handle: resident structures, graph-captured generations."""
+
+    def __init__(self, handle, n_pop, n_structs, width):
+        self.handle = handle
+        self.n_pop, self.n_structs, self.width = n_pop, n_structs, width
+
+    def eval(self, params, want_out=False):
+        prm = np.ascontiguousarray(params, dtype=np.float32)
+        assert prm.shape[0] == self.n_pop
+        rmse = np.zeros(self.n_pop)
+        out = np.zeros((self.n_pop, self.n_structs, self.width)) if want_out else None
+        _check(_lib.tnep_population_eval(self.handle, prm.ctypes.data, rmse.ctypes.data,
+                                         out.ctypes.data if want_out else None))
+        return rmse, out
+
+    def info(self):
+        v = np.zeros(8)
+        _check(_lib.tnep_population_info(self.handle, v.ctypes.data))
+        return dict(block=int(v[0]), pop_major=int(v[1]), tune_ms=v[2:6].tolist(), last_ms=v[6], atoms=int(v[7]))
+
+    def close(self):
+        if self.handle:
+            _lib.tnep_population_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tnep_population_create(ctx: Context, model: int, params, offsets, pos, box, types, target) -> Population:
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    T = _Buf(types, np.int32, "types")
+    TG = _Buf(target, np.float64, "target")
+    h = C.c_void_p()
+    _check(_lib.tnep_population_create(ctx.handle, int(model), prm.shape[0], prm.ctypes.data, S,
+                                       offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr, T.ptr, TG.ptr,
+                                       C.byref(h)))
+    return Population(h, prm.shape[0], S, ctx.dims[model])

@@ -365,3 +365,34 @@ def test_dense_cluster_large_lists(tn):
         assert np.linalg.norm(got[0] - r.tensor) <= max(REL * np.linalg.norm(r.tensor),
                                                         COND * np.abs(r.per_atom).sum())
     ctx.close()
+
+
+def test_population_graph_replay_and_shapes(tn):
+    """Graph-captured generations equal the one-shot population call, for every
+    launch shape the autotuner may pick, and for new parameters each time."""
+    rng = np.random.default_rng(8)
+    structs = synth.population_structures(n_clusters=10, n_boxes=4, seed_k=2)
+    bt = synth.concat_structures(structs)
+    hp = synth.HyperParams(n_types=2, rank=2)
+    P = 6
+    sc = synth.default_q_scaler(hp)
+    target = rng.standard_normal((bt.n_structs, 9))
+    params = [np.stack([synth.model_params(hp, rng) for _ in range(P)]) for _ in range(2)]
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0][0], sc)], 2, RC)
+    pop = tn.tnep_population_create(ctx, 0, params[0], bt.offsets, bt.pos, bt.box, bt.types, target)
+    info = pop.info()
+    assert info["block"] in (64, 128) and info["atoms"] == len(bt.types)
+    assert all(t > 0 for t in info["tune_ms"])
+    for prm in params:  # two generations with different parameters
+        rmse, pred = pop.eval(prm, want_out=True)
+        r1, p1 = tn.tnep_eval_population(ctx, 0, prm, bt.offsets, bt.pos, bt.box, bt.types, target, want_out=True)
+        np.testing.assert_allclose(pred, p1, rtol=0, atol=1e-12 * np.abs(p1).max())
+        np.testing.assert_allclose(rmse, r1, rtol=1e-12)
+    c1 = tn.tnep_create([tn.Model.from_hyper(hp, params[1][0], sc)], 2, RC)
+    for block in (64, 128):  # the CTA size does not change any arithmetic
+        tn.tnep_set_option(c1, tn.TNEP_OPT_BLOCK_ATOMS, block)
+        (ref,), _ = tn.tnep_eval_batch(c1, bt.offsets, bt.pos, bt.box, bt.types)
+        assert np.array_equal(pred[0], ref)
+    c1.close()
+    pop.close()
+    ctx.close()
