@@ -202,6 +202,41 @@ def serving_bench(tn, synth, device, rates, n_req):
             "mean_atoms": float(atoms.mean()), "rates": out}
 
 
+def population_bench(tn, synth, device, n_pop=50, gens=5):
+    """50 parameter vectors x 600 uneven structures per generation (open water
+    clusters of 3-300 atoms, periodic boxes of 192-1,536 atoms), dipole RMSE
+    against seeded random targets; structures resident, generations replayed
+    from a CUDA graph with the autotuned launch shape."""
+    rng = np.random.default_rng(synth.seed_for(4, 9))
+    structs = synth.population_structures()
+    bt = synth.concat_structures(structs)
+    hp = synth.HyperParams(n_types=2, rank=1)
+    sc = synth.default_q_scaler(hp)
+    target = rng.standard_normal((bt.n_structs, 3))
+    gen_params = [np.stack([synth.model_params(hp, rng) for _ in range(n_pop)]) for _ in range(gens + 1)]
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, gen_params[0][0], sc)], 2, RC, device=device)
+    pop = tn.tnep_population_create(ctx, 0, gen_params[0], bt.offsets, bt.pos, bt.box, bt.types, target)
+    pop.eval(gen_params[0])
+    t0 = time.perf_counter()
+    dev_ms = 0.0
+    for g_ in range(1, gens + 1):
+        rmse, _ = pop.eval(gen_params[g_])
+        dev_ms += pop.info()["last_ms"]
+    wall = (time.perf_counter() - t0) / gens
+    info = pop.info()
+    t1 = time.perf_counter()
+    tn.tnep_eval_population(ctx, 0, gen_params[1], bt.offsets, bt.pos, bt.box, bt.types, target)
+    oneshot = time.perf_counter() - t1
+    pop.close()
+    ctx.close()
+    atoms = len(bt.types)
+    return {"workload": f"{n_pop} parameter vectors x {bt.n_structs} structures ({atoms} atoms), rank 1",
+            "generation_ms": wall * 1e3, "generation_device_ms": dev_ms / gens,
+            "atom_evals_per_s": n_pop * atoms / wall, "oneshot_ms": oneshot * 1e3,
+            "chosen": {"atoms_per_cta": info["block"], "individual_major": info["pop_major"]},
+            "candidates_ms": info["tune_ms"], "rmse_first": float(rmse[0])}
+
+
 # ------------------------------------------------------------------ multi-rank
 def shard_seed_k(rank: int) -> int:
     """Each rank evaluates its own trajectory (weak scaling over frames):
@@ -266,6 +301,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rates", default="1000,5000")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-population", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -387,6 +423,8 @@ def main():
                      "fused_launches_per_step": fused_launches / args.steps},
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_population:
+        line["population"] = population_bench(tn, synth, local)
     if rank == 0 and not args.no_serve:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["served"] = serving_bench(tn, synth, local, rates, args.serve_requests)
