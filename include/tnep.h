@@ -95,7 +95,8 @@ typedef struct {
   const float* params;
   size_t n_params;
   const float* q_scaler;  /* [D] multiplies q before the network, or NULL = ones */
-  int mlp_precision;      /* 0 = FP32, 1 = BF16 tensor-core MLP with FP32 accumulation */
+  int mlp_precision;      /* 0 = FP32; 1 = network products on the tensor cores (tcgen05) in BF16 with
+                             FP32 accumulation (descriptor dimension <= 32, n_hidden <= 32) */
 } tnep_model_desc;
 
 /* Creates a context on `device` holding `n_models` models that share the

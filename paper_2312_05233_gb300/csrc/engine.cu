@@ -105,7 +105,11 @@ tnep_status validate_model(const tnep_model_desc& d, int T) {
   if (variant_of(d.n_max_R + 1, d.n_max_A + 1, d.basis_R + 1, d.basis_A + 1, d.l_max, d.use_4body) < 0)
     return fail(TNEP_ERR_UNSUPPORTED, "no compiled kernel for these descriptor sizes");
   if (d.mlp_precision != 0 && d.mlp_precision != 1) return fail(TNEP_ERR_INVALID, "mlp_precision must be 0 or 1");
-  if (d.mlp_precision == 1) return fail(TNEP_ERR_UNSUPPORTED, "BF16 tensor-core MLP not built in this library");
+  if (d.mlp_precision == 1) {
+    const int D = (d.n_max_R + 1) + (d.n_max_A + 1) * (d.l_max + (d.use_4body ? 1 : 0));
+    if (D > 32 || d.n_hidden > 32)
+      return fail(TNEP_ERR_UNSUPPORTED, "the tensor-core network takes at most 32 descriptor components and 32 hidden units");
+  }
   const size_t want = expected_params(d, T);
   if (d.n_params != want)
     return fail(TNEP_ERR_INVALID, "n_params " + std::to_string(d.n_params) + " != layout " + std::to_string(want));
@@ -233,6 +237,7 @@ FusedArgs fused_args(tnep_ctx* c, Workspace& w, const Model& m, int N) {
   f.mom_stride = w.atom_stride;
   f.v0 = w.mom_v0;
   f.w0 = w.mom_w0;
+  f.status = w.d_status;
   f.nbr_A = w.nbr_A.p;
   f.cnt_A = w.cnt_A.p;
   f.cap_A = w.cap_A;
@@ -289,7 +294,7 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
     FusedArgs f = fused_args(c, w, m, N);
     f.per_atom = w.per_atom.p + k * per_model;
     f.per_atom_stride = 0;
-    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, st));
+    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, m.d.mlp_precision == 1, st));
   }
   if (ev_done) TNEP_CUDA(cudaEventRecord(ev_done, st));
   TNEP_CUDA(w.partial.ensure((size_t)std::max(S, 1) * reduce_chunks(w.max_atoms) * 9));

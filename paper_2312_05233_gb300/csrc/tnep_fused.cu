@@ -30,6 +30,7 @@
 
 #include <atomic>
 
+#include "tc_sm100.cuh"
 #include "tnep_device.cuh"
 #include "tnep_internal.cuh"
 
@@ -184,8 +185,18 @@ __device__ __forceinline__ float trace_m3(const float* a, float* grad) {
   return tr;
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK>
+// Bytes of shared memory the tensor-core network needs after the scratch:
+// mbarrier + TMEM slot (128 B), the A tile (128 x 32 bf16) and, per network,
+// the two B tiles (32 x 32 bf16 each).
+__host__ __device__ constexpr int tc_smem_bytes(int nets) { return 128 + 128 * 32 * 2 + nets * 2 * 32 * 32 * 2; }
+__host__ __device__ constexpr uint32_t tc_tmem_cols(int nets) {
+  return nets * 32 <= 32 ? 32u : nets * 32 <= 64 ? 64u : nets * 32 <= 128 ? 128u : 256u;
+}
+constexpr long long kMbarTries = 1LL << 22;
+
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, bool TC>
 __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant__ FusedArgs a) {
+  static_assert(!TC || BLK == 128, "the tensor-core network uses M = 128 rows, one per atom");
   constexpr int NLM = LMAX * (LMAX + 2);
   constexpr int D = NR + NA * LMAX + (FB ? NA : 0);
   constexpr int DP = (D + 3) & ~3;
@@ -206,8 +217,49 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   __syncthreads();
   const int tid = threadIdx.x;
   float* scratch = sm + Ly.words + tid;  // slot s at scratch[s * BLK]
-  const int i = ablk * BLK + tid;
-  if (i >= a.n_atoms) return;
+  const int i_raw = ablk * BLK + tid;
+  const bool valid = i_raw < a.n_atoms;
+  // The tensor-core path has CTA-wide barriers: threads past the end work on
+  // the last atom and store nothing.
+  if (!TC && !valid) return;
+  const int i = valid ? i_raw : a.n_atoms - 1;
+
+  // ---------------------------------------------------------------- tensor-core set-up
+  uint32_t tmem_base = 0, mbar = 0;
+  __nv_bfloat16* tileA = nullptr;
+  const __nv_bfloat16* tileB1 = nullptr;
+  const __nv_bfloat16* tileB2 = nullptr;
+  if constexpr (TC) {
+    constexpr int NSLOT = NA * LMAX * (LMAX + 2);
+    unsigned char* tcb = reinterpret_cast<unsigned char*>(sm + Ly.words + NSLOT * BLK);
+    uint64_t* mb = reinterpret_cast<uint64_t*>(tcb);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(tcb + 8);
+    tileA = reinterpret_cast<__nv_bfloat16*>(tcb + 128);
+    __nv_bfloat16* B1 = tileA + 128 * 32;
+    __nv_bfloat16* B2 = B1 + Ly.nets * 32 * 32;
+    // B1[net]: row = hidden unit h, column = descriptor d  (W0[h][d])
+    // B2[net]: row = descriptor d, column = hidden unit h  (W0[h][d])
+    for (int idx = tid; idx < Ly.nets * 32 * 32; idx += BLK) {
+      const int nt = idx >> 10, r = (idx >> 5) & 31, k = idx & 31;
+      const float* W = sm + Ly.off_W0 + nt * Ly.H * DP;
+      const float w1v = (r < Ly.H && k < Ly.D) ? W[r * DP + k] : 0.f;
+      const float w2v = (k < Ly.H && r < Ly.D) ? W[k * DP + r] : 0.f;
+      B1[nt * 1024 + (tc::kmajor_offset(r, k, 32) >> 1)] = __float2bfloat16_rn(w1v);
+      B2[nt * 1024 + (tc::kmajor_offset(r, k, 32) >> 1)] = __float2bfloat16_rn(w2v);
+    }
+    if (tid == 0) {
+      tc::mbar_init(tc::smem_addr(mb), 1);
+      tc::fence_mbar_init();
+    }
+    if (tid < 32) tc::tmem_alloc(tc::smem_addr(slot), tc_tmem_cols(Ly.nets));
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tmem_base = *slot;
+    mbar = tc::smem_addr(mb);
+    tileB1 = B1;
+    tileB2 = B2;
+  }
 
   const float4 pi = a.pos4[i];
   const int ti = __float_as_int(pi.w);
@@ -293,7 +345,80 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   const float* sc = sm + Ly.off_scaler;
   float e[DP];
   float U = -sm[Ly.off_b1 + net];
-  {
+  if constexpr (TC) {
+    // z = W0 s on the tensor cores: A = s (bf16, one row per atom), B1 = W0,
+    // D (F32) in TMEM columns [32 net, 32 net + 32); then e = W0^T v likewise.
+    static_assert(DP <= 32, "the tensor-core network takes at most 32 descriptor components");
+    const int warp = tid >> 5;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+    const uint32_t a_base = tc::smem_addr(tileA);
+    auto write_row = [&](const float* v) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        __nv_bfloat162 h2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h2[u] = __floats2bfloat162_rn(v[8 * c + 2 * u], v[8 * c + 2 * u + 1]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(tileA) + tc::kmajor_offset(tid, 8 * c, 32)) =
+            *reinterpret_cast<uint4*>(h2);
+      }
+    };
+    auto gemm = [&](const __nv_bfloat16* B, uint32_t parity) -> bool {
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int t = 0; t < Ly.nets; ++t)
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+            tc::mma_bf16(tmem_base + 32 * t, tc::smem_desc(a_base + 256 * ks, 128, 512),
+                         tc::smem_desc(tc::smem_addr(B + t * 1024) + 256 * ks, 128, 512), idesc, ks);
+        tc::commit_to(mbar);
+      }
+      const bool ok = tc::mbar_wait_bounded(mbar, parity, kMbarTries);
+      tc::fence_after_sync();
+      return ok;
+    };
+    auto read_row = [&](float* v) {
+      for (int t = 0; t < Ly.nets; ++t) {
+        float r[32];
+        tc::tmem_ld32(tmem_base + ((uint32_t)(32 * warp) << 16) + 32 * t, r);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = (t == net) ? r[k] : v[k];
+      }
+    };
+    float buf[32];
+#pragma unroll
+    for (int d = 0; d < 32; ++d) buf[d] = d < DP ? q[d] * sc[d] : 0.f;
+    write_row(buf);
+    bool ok = gemm(tileB1, 0);
+    float z[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) z[k] = 0.f;
+    read_row(z);
+#pragma unroll
+    for (int h = 0; h < 32; ++h) {
+      if (h < Ly.H) {
+        const float hh = tanhf(z[h] - b0[h]);
+        const float wh = w1[h];
+        U += wh * hh;
+        buf[h] = wh * (1.f - hh * hh);
+      } else {
+        buf[h] = 0.f;
+      }
+    }
+    write_row(buf);
+    ok = gemm(tileB2, 1) && ok;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) z[k] = 0.f;
+    read_row(z);
+#pragma unroll
+    for (int d = 0; d < DP; ++d) e[d] = z[d] * sc[d];
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
+    if (!ok && a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
+  } else {
     float s[DP];
 #pragma unroll
     for (int d = 0; d < DP; ++d) { s[d] = q[d] * sc[d]; e[d] = 0.f; }
@@ -422,18 +547,19 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   }
 
   // ---------------------------------------------------------------- per-atom output
+  if (!valid) return;
   float* out = a.per_atom + (size_t)pop * a.per_atom_stride;
   if constexpr (RANK == 2) { acc[0] += U; acc[4] += U; acc[8] += U; }
 #pragma unroll
   for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK>
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, bool TC>
 cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
   const int nblk = (a.n_atoms + BLK - 1) / BLK;
   if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
-  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK> : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK>;
+  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TC> : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TC>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, BLK, smem, st>>>(a);
@@ -441,9 +567,11 @@ cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, c
 }
 
 template <int NR, int NA, int BR, int BA, int LMAX, bool FB>
-cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, size_t smem, cudaStream_t st) {
-  if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64>(rank, a, n_pop, smem, st);
-  return launch_block<NR, NA, BR, BA, LMAX, FB, 128>(rank, a, n_pop, smem, st);
+cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, bool tc, size_t smem,
+                           cudaStream_t st) {
+  if (tc) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, true>(rank, a, n_pop, smem, st);
+  if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64, false>(rank, a, n_pop, smem, st);
+  return launch_block<NR, NA, BR, BA, LMAX, FB, 128, false>(rank, a, n_pop, smem, st);
 }
 
 // Per-structure FP64 sums in two deterministic stages: CTA (s, chunk) sums a
@@ -530,21 +658,23 @@ int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb) {
   return -1;
 }
 
-size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block) {
+size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, bool tc) {
   int slots = 0;
   if (variant == kVarStd) slots = 5 * 24;
   if (variant == kVarSmall) slots = 3 * 15;
-  return (size_t)(lay.words + slots * block) * sizeof(float);
+  if (tc) block = 128;
+  return (size_t)(lay.words + slots * block) * sizeof(float) + (tc ? tc_smem_bytes(lay.nets) : 0);
 }
 
-cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, cudaStream_t st) {
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, bool tc,
+                         cudaStream_t st) {
   if (a.n_atoms <= 0 || n_pop <= 0) return cudaSuccess;
   if (block != 64 && block != 128) return cudaErrorInvalidValue;
   count_launches(1);
-  const size_t smem = fused_smem_bytes(variant, a.lay, block);
+  const size_t smem = fused_smem_bytes(variant, a.lay, block, tc);
   switch (variant) {
-    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, block, smem, st);
-    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, block, smem, st);
+    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, block, tc, smem, st);
+    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, block, tc, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -138,14 +138,16 @@ struct FusedArgs {
   size_t per_atom_stride;    // floats between individuals
   int atom_stride;           // row stride of the SoA output
   int pop_major;             // 1: blockIdx.x = individual, blockIdx.y = atom block
+  DevStatus* status;         // error word (bounded waits of the tensor-core path)
 };
 
 // Kernel variant keys (must match the compiled instantiations).
 enum Variant { kVarStd = 0, kVarSmall = 1, kVarCount = 2 };
 
 int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb);
-size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block);
-cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, cudaStream_t st);
+// tc: network on the tensor cores in BF16 with FP32 accumulation (128 atoms per CTA).
+size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, bool tc);
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, bool tc, cudaStream_t st);
 
 // Per-structure FP64 reduction of per-atom contributions.  `max_atoms` is
 // the largest structure; `partial` holds n_pop * n_structs * reduce_chunks(max_atoms) * C doubles.

@@ -396,3 +396,63 @@ def test_population_graph_replay_and_shapes(tn):
     c1.close()
     pop.close()
     ctx.close()
+
+
+# ------------------------------------------------- BF16 tensor-core network
+BF16_REL = 1e-3
+BF16_COND = 1e-4
+
+
+@pytest.mark.parametrize("small,n_types", [(False, 2), (True, 3)])
+def test_bf16_tensor_core_network(tn, small, n_types):
+    """Network products on tcgen05 (BF16 operands, FP32 accumulation) against
+    the FP64 oracle at the BF16 bar (1e-3 relative per frame), and close to
+    the FP32 path."""
+    if n_types == 2:
+        frames, types, box = synth.water_small(6)
+    else:
+        rng = np.random.default_rng(6)
+        base, types, box = synth.bzo_supercell(3)
+        frames = synth.thermal_frames(base, box, 4, 0.08, rng)
+        box = box.astype(np.float32)
+    ms32, om = models_for(tn, n_types, small=small)
+    ms16 = [tn.Model.from_hyper(synth.HyperParams(n_types=n_types, rank=m.rank, n_max_R=m.n_max_R,
+                                                  n_max_A=m.n_max_A, basis_R=m.basis_R, basis_A=m.basis_A,
+                                                  l_max=m.l_max, use_4body=m.use_4body, n_hidden=m.n_hidden),
+                                m.params, m.q_scaler, mlp_precision=1) for m in ms32]
+    c32 = tn.tnep_create(ms32, n_types, RC)
+    c16 = tn.tnep_create(ms16, n_types, RC)
+    o32 = tn.tnep_eval(c32, frames, box, types)
+    o16 = tn.tnep_eval(c16, frames, box, types)
+    for g16, g32, m in zip(o16, o32, om):
+        for f in range(len(frames)):
+            r = oracle.evaluate(m, frames[f], box, types)
+            scale = np.linalg.norm(r.tensor)
+            cond = np.abs(r.per_atom).sum()
+            assert np.linalg.norm(g16[f] - r.tensor) <= max(BF16_REL * scale, BF16_COND * cond)
+            assert np.linalg.norm(g32[f] - r.tensor) <= max(REL * scale, COND * cond)
+        assert not np.array_equal(g16, g32)  # the tensor-core path really ran
+    c32.close()
+    c16.close()
+
+
+def test_bf16_population_and_tail_block(tn):
+    """Tensor-core path with a partial last CTA and in the population kernel."""
+    rng = np.random.default_rng(12)
+    structs = synth.population_structures(n_clusters=5, n_boxes=2, seed_k=3)
+    bt = synth.concat_structures(structs)
+    assert len(bt.types) % 128 != 0
+    hp = synth.HyperParams(n_types=2, rank=1)
+    sc = synth.default_q_scaler(hp)
+    params = np.stack([synth.model_params(hp, rng) for _ in range(3)])
+    target = rng.standard_normal((bt.n_structs, 3))
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc, mlp_precision=1)], 2, RC)
+    rmse, pred = tn.tnep_eval_population(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target,
+                                         want_out=True)
+    om = oracle.OracleModel.from_flat(hp, params[1], sc, *RC)
+    for s in range(bt.n_structs):
+        a0, a1 = bt.offsets[s], bt.offsets[s + 1]
+        r = oracle.evaluate(om, bt.pos[a0:a1], bt.box[s], bt.types[a0:a1])
+        assert np.linalg.norm(pred[1][s] - r.tensor) <= max(BF16_REL * np.linalg.norm(r.tensor),
+                                                            BF16_COND * np.abs(r.per_atom).sum())
+    ctx.close()
