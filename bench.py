@@ -49,13 +49,13 @@ def workload_config(n_frames):
     }
 
 
-def make_models(tn, synth):
+def make_models(tn, synth, mlp_precision=0):
     rng = np.random.default_rng(synth.seed_for(2, 1))
     out, hps, params = [], [], []
     for rank in (1, 2):
         hp = synth.HyperParams(n_types=2, rank=rank)
         p = synth.model_params(hp, rng)
-        out.append(tn.Model.from_hyper(hp, p, synth.default_q_scaler(hp)) if tn else None)
+        out.append(tn.Model.from_hyper(hp, p, synth.default_q_scaler(hp), mlp_precision) if tn else None)
         hps.append(hp)
         params.append(p)
     return out, hps, params
@@ -302,6 +302,7 @@ def main():
     ap.add_argument("--serve-rates", default="1000,5000")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-population", action="store_true")
+    ap.add_argument("--mlp-precision", type=int, default=0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -328,7 +329,7 @@ def main():
     # each rank evaluates its own trajectory (weak scaling over frames)
     frames, types, box = synth.water_bulk(n_frames=args.frames, seed_k=shard_seed_k(rank))
     F, N = frames.shape[0], frames.shape[1]
-    models, hps, params = make_models(tn, synth)
+    models, hps, params = make_models(tn, synth, args.mlp_precision)
     ctx = tn.tnep_create(models, 2, RC, device=local)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
