@@ -95,8 +95,12 @@ typedef struct {
   const float* params;
   size_t n_params;
   const float* q_scaler;  /* [D] multiplies q before the network, or NULL = ones */
-  int mlp_precision;      /* 0 = FP32; 1 = network products on the tensor cores (tcgen05) in BF16 with
-                             FP32 accumulation (descriptor dimension <= 32, n_hidden <= 32) */
+  int mlp_precision;      /* network products W0 s and W0^T v: 0 = FP32 on the CUDA cores;
+                             1 = tensor cores (tcgen05), activations and weights rounded to BF16,
+                             FP32 accumulation in tensor memory (relative error ~2^-8);
+                             2 = tensor cores, both operands split into high + low BF16 parts,
+                             three products hi*hi + hi*lo + lo*hi (error ~2^-17).
+                             1 and 2 need descriptor dimension <= 32 and n_hidden <= 32. */
 } tnep_model_desc;
 
 /* Creates a context on `device` holding `n_models` models that share the

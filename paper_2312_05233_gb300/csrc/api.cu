@@ -92,7 +92,7 @@ tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types
     c->models.push_back(std::move(m));
     if (e != cudaSuccess) return bail(cuda_fail(e, "model upload"));
     if (fused_smem_bytes(c->models.back().variant, c->models.back().lay, kFusedBlockMax,
-                         c->models.back().d.mlp_precision == 1) > 227 * 1024)
+                         c->models.back().d.mlp_precision) > 227 * 1024)
       return bail(fail(TNEP_ERR_UNSUPPORTED, "model too large for shared memory"));
   }
   *out = c;
@@ -422,7 +422,7 @@ tnep_status tnep_eval_population(tnep_ctx* c, int model, int n_pop, const float*
     f.per_atom_stride = pa_pop;
     cudaEvent_t* ev = nullptr;
     TNEP_TRY(pass_events(c, 0, &ev));
-    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, n_pop, c->block_atoms, m.d.mlp_precision == 1, st));
+    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, n_pop, c->block_atoms, m.d.mlp_precision, st));
     TNEP_CUDA(cudaEventRecord(ev[2], st));
     TNEP_CUDA(w.partial.ensure((size_t)n_pop * n_structs * reduce_chunks(w.max_atoms) * m.C));
     TNEP_CUDA(launch_reduce(n_structs, n_pop, w.offsets.p, w.max_atoms, w.per_atom.p, pa_pop, w.atom_stride, m.C,

@@ -104,8 +104,8 @@ tnep_status validate_model(const tnep_model_desc& d, int T) {
     return fail(TNEP_ERR_INVALID, "negative descriptor size");
   if (variant_of(d.n_max_R + 1, d.n_max_A + 1, d.basis_R + 1, d.basis_A + 1, d.l_max, d.use_4body) < 0)
     return fail(TNEP_ERR_UNSUPPORTED, "no compiled kernel for these descriptor sizes");
-  if (d.mlp_precision != 0 && d.mlp_precision != 1) return fail(TNEP_ERR_INVALID, "mlp_precision must be 0 or 1");
-  if (d.mlp_precision == 1) {
+  if (d.mlp_precision < 0 || d.mlp_precision > 2) return fail(TNEP_ERR_INVALID, "mlp_precision must be 0, 1 or 2");
+  if (d.mlp_precision != 0) {
     const int D = (d.n_max_R + 1) + (d.n_max_A + 1) * (d.l_max + (d.use_4body ? 1 : 0));
     if (D > 32 || d.n_hidden > 32)
       return fail(TNEP_ERR_UNSUPPORTED, "the tensor-core network takes at most 32 descriptor components and 32 hidden units");
@@ -294,7 +294,7 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
     FusedArgs f = fused_args(c, w, m, N);
     f.per_atom = w.per_atom.p + k * per_model;
     f.per_atom_stride = 0;
-    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, m.d.mlp_precision == 1, st));
+    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, m.d.mlp_precision, st));
   }
   if (ev_done) TNEP_CUDA(cudaEventRecord(ev_done, st));
   TNEP_CUDA(w.partial.ensure((size_t)std::max(S, 1) * reduce_chunks(w.max_atoms) * 9));

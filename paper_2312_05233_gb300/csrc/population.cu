@@ -62,7 +62,7 @@ tnep_status enqueue_generation(tnep_population* p, bool with_copies) {
     TNEP_CUDA(cudaMemcpyAsync(p->d_params.p, p->h_params.p, sizeof(float) * (size_t)p->n_pop * m.lay.words,
                               cudaMemcpyHostToDevice, st));
   FusedArgs f = pop_args(p);
-  TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, p->n_pop, p->block, m.d.mlp_precision == 1, st));
+  TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, p->n_pop, p->block, m.d.mlp_precision, st));
   TNEP_CUDA(launch_reduce(p->S, p->n_pop, p->ws.offsets.p, p->ws.max_atoms, p->ws.per_atom.p, f.per_atom_stride,
                           p->ws.atom_stride, m.C, p->ws.partial.p, p->d_pred.p, (size_t)p->S * m.C, st));
   TNEP_CUDA(launch_rmse(p->n_pop, p->S, m.C, p->d_pred.p, p->d_target.p, p->d_rmse.p, st));
@@ -95,7 +95,7 @@ tnep_status autotune(tnep_population* p) {
       p->block = b;
       p->pop_major = order;
       const int nblk = (p->N + b - 1) / b;
-      const bool tc = p->ctx->models[p->model].d.mlp_precision == 1;
+      const bool tc = p->ctx->models[p->model].d.mlp_precision != 0;
       if ((order == 1 && nblk > 65535) || (tc && b != 128)) { p->tune_ms[idx] = -1; continue; }
       TNEP_TRY(enqueue_generation(p, false));  // warm-up
       TNEP_CUDA(cudaEventRecord(p->ev0, p->stream));

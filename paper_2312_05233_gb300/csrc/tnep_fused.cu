@@ -186,16 +186,22 @@ __device__ __forceinline__ float trace_m3(const float* a, float* grad) {
 }
 
 // Bytes of shared memory the tensor-core network needs after the scratch:
-// mbarrier + TMEM slot (128 B), the A tile (128 x 32 bf16) and, per network,
-// the two B tiles (32 x 32 bf16 each).
-__host__ __device__ constexpr int tc_smem_bytes(int nets) { return 128 + 128 * 32 * 2 + nets * 2 * 32 * 32 * 2; }
+// mbarrier + TMEM slot (128 B), the A tile (128 rows x 64: a high and a low
+// bf16 part of 32 columns each) and, per network, the two B tiles (32 rows x
+// 64, high and low parts of the weights).
+__host__ __device__ constexpr int tc_smem_bytes(int nets) { return 128 + 128 * 64 * 2 + nets * 2 * 32 * 64 * 2; }
 __host__ __device__ constexpr uint32_t tc_tmem_cols(int nets) {
   return nets * 32 <= 32 ? 32u : nets * 32 <= 64 ? 64u : nets * 32 <= 128 ? 128u : 256u;
 }
 constexpr long long kMbarTries = 1LL << 22;
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, bool TC>
+// TCM: 0 = FP32 network on the CUDA cores; 1 = network products on the
+// tensor cores with BF16 operands and FP32 accumulation; 2 = the same with
+// every operand split into a high and a low BF16 part and three products
+// (hi*hi + hi*lo + lo*hi), which is accurate to about 2^-17.
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, int TCM>
 __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant__ FusedArgs a) {
+  constexpr bool TC = TCM != 0;
   static_assert(!TC || BLK == 128, "the tensor-core network uses M = 128 rows, one per atom");
   constexpr int NLM = LMAX * (LMAX + 2);
   constexpr int D = NR + NA * LMAX + (FB ? NA : 0);
@@ -235,17 +241,22 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     uint64_t* mb = reinterpret_cast<uint64_t*>(tcb);
     uint32_t* slot = reinterpret_cast<uint32_t*>(tcb + 8);
     tileA = reinterpret_cast<__nv_bfloat16*>(tcb + 128);
-    __nv_bfloat16* B1 = tileA + 128 * 32;
-    __nv_bfloat16* B2 = B1 + Ly.nets * 32 * 32;
+    __nv_bfloat16* B1 = tileA + 128 * 64;
+    __nv_bfloat16* B2 = B1 + Ly.nets * 32 * 64;
     // B1[net]: row = hidden unit h, column = descriptor d  (W0[h][d])
     // B2[net]: row = descriptor d, column = hidden unit h  (W0[h][d])
+    // columns 0-31 hold the bf16 rounding of the weight, 32-63 the bf16
+    // rounding of what is left over
     for (int idx = tid; idx < Ly.nets * 32 * 32; idx += BLK) {
       const int nt = idx >> 10, r = (idx >> 5) & 31, k = idx & 31;
       const float* W = sm + Ly.off_W0 + nt * Ly.H * DP;
       const float w1v = (r < Ly.H && k < Ly.D) ? W[r * DP + k] : 0.f;
       const float w2v = (k < Ly.H && r < Ly.D) ? W[k * DP + r] : 0.f;
-      B1[nt * 1024 + (tc::kmajor_offset(r, k, 32) >> 1)] = __float2bfloat16_rn(w1v);
-      B2[nt * 1024 + (tc::kmajor_offset(r, k, 32) >> 1)] = __float2bfloat16_rn(w2v);
+      const __nv_bfloat16 h1 = __float2bfloat16_rn(w1v), h2 = __float2bfloat16_rn(w2v);
+      B1[nt * 2048 + (tc::kmajor_offset(r, k, 64) >> 1)] = h1;
+      B1[nt * 2048 + (tc::kmajor_offset(r, 32 + k, 64) >> 1)] = __float2bfloat16_rn(w1v - __bfloat162float(h1));
+      B2[nt * 2048 + (tc::kmajor_offset(r, k, 64) >> 1)] = h2;
+      B2[nt * 2048 + (tc::kmajor_offset(r, 32 + k, 64) >> 1)] = __float2bfloat16_rn(w2v - __bfloat162float(h2));
     }
     if (tid == 0) {
       tc::mbar_init(tc::smem_addr(mb), 1);
@@ -352,27 +363,42 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     const int warp = tid >> 5;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
     const uint32_t a_base = tc::smem_addr(tileA);
+    // row `tid` of A: columns 0-31 the bf16 rounding of v, 32-63 the remainder
     auto write_row = [&](const float* v) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        __nv_bfloat162 h2[4];
+        __nv_bfloat162 hi[4], lo[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) h2[u] = __floats2bfloat162_rn(v[8 * c + 2 * u], v[8 * c + 2 * u + 1]);
-        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(tileA) + tc::kmajor_offset(tid, 8 * c, 32)) =
-            *reinterpret_cast<uint4*>(h2);
+        for (int u = 0; u < 4; ++u) {
+          const float x0 = v[8 * c + 2 * u], x1 = v[8 * c + 2 * u + 1];
+          hi[u] = __floats2bfloat162_rn(x0, x1);
+          lo[u] = __floats2bfloat162_rn(x0 - __low2float(hi[u]), x1 - __high2float(hi[u]));
+        }
+        unsigned char* base = reinterpret_cast<unsigned char*>(tileA);
+        *reinterpret_cast<uint4*>(base + tc::kmajor_offset(tid, 8 * c, 64)) = *reinterpret_cast<uint4*>(hi);
+        if constexpr (TCM == 2)
+          *reinterpret_cast<uint4*>(base + tc::kmajor_offset(tid, 32 + 8 * c, 64)) = *reinterpret_cast<uint4*>(lo);
       }
     };
+    // D = sum over (A block, B block) pairs: TCM 1: (hi, hi) -- plain BF16
+    // operands; TCM 2: (hi, hi) + (hi, lo) + (lo, hi) -- both operands to ~2^-17.
     auto gemm = [&](const __nv_bfloat16* B, uint32_t parity) -> bool {
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       __syncthreads();
       if (tid == 0) {
         tc::fence_after_sync();
-        for (int t = 0; t < Ly.nets; ++t)
+        constexpr int NPAIR = TCM == 2 ? 3 : 1;
+        const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+        for (int t = 0; t < Ly.nets; ++t) {
+          const uint32_t b_base = tc::smem_addr(B + t * 2048);
+          int step = 0;
+          for (int q2 = 0; q2 < NPAIR; ++q2)
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks)
-            tc::mma_bf16(tmem_base + 32 * t, tc::smem_desc(a_base + 256 * ks, 128, 512),
-                         tc::smem_desc(tc::smem_addr(B + t * 1024) + 256 * ks, 128, 512), idesc, ks);
+            for (int ks = 0; ks < 2; ++ks, ++step)
+              tc::mma_bf16(tmem_base + 32 * t, tc::smem_desc(a_base + 512 * pa[q2] + 256 * ks, 128, 1024),
+                           tc::smem_desc(b_base + 512 * pb[q2] + 256 * ks, 128, 1024), idesc, step > 0);
+        }
         tc::commit_to(mbar);
       }
       const bool ok = tc::mbar_wait_bounded(mbar, parity, kMbarTries);
@@ -554,12 +580,12 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, bool TC>
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, int TCM>
 cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
   const int nblk = (a.n_atoms + BLK - 1) / BLK;
   if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
-  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TC> : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TC>;
+  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TCM> : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TCM>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, BLK, smem, st>>>(a);
@@ -567,11 +593,12 @@ cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, c
 }
 
 template <int NR, int NA, int BR, int BA, int LMAX, bool FB>
-cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, bool tc, size_t smem,
+cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, int tcm, size_t smem,
                            cudaStream_t st) {
-  if (tc) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, true>(rank, a, n_pop, smem, st);
-  if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64, false>(rank, a, n_pop, smem, st);
-  return launch_block<NR, NA, BR, BA, LMAX, FB, 128, false>(rank, a, n_pop, smem, st);
+  if (tcm == 1) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 1>(rank, a, n_pop, smem, st);
+  if (tcm == 2) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 2>(rank, a, n_pop, smem, st);
+  if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64, 0>(rank, a, n_pop, smem, st);
+  return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 0>(rank, a, n_pop, smem, st);
 }
 
 // Per-structure FP64 sums in two deterministic stages: CTA (s, chunk) sums a
@@ -658,7 +685,8 @@ int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb) {
   return -1;
 }
 
-size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, bool tc) {
+size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, int tcm) {
+  const bool tc = tcm != 0;
   int slots = 0;
   if (variant == kVarStd) slots = 5 * 24;
   if (variant == kVarSmall) slots = 3 * 15;
@@ -666,15 +694,16 @@ size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, bool tc)
   return (size_t)(lay.words + slots * block) * sizeof(float) + (tc ? tc_smem_bytes(lay.nets) : 0);
 }
 
-cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, bool tc,
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, int tcm,
                          cudaStream_t st) {
   if (a.n_atoms <= 0 || n_pop <= 0) return cudaSuccess;
   if (block != 64 && block != 128) return cudaErrorInvalidValue;
+  if (tcm < 0 || tcm > 2) return cudaErrorInvalidValue;
   count_launches(1);
-  const size_t smem = fused_smem_bytes(variant, a.lay, block, tc);
+  const size_t smem = fused_smem_bytes(variant, a.lay, block, tcm);
   switch (variant) {
-    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, block, tc, smem, st);
-    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, block, tc, smem, st);
+    case kVarStd: return launch_variant<5, 5, 9, 9, 4, true>(rank, a, n_pop, block, tcm, smem, st);
+    case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, block, tcm, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -145,9 +145,11 @@ struct FusedArgs {
 enum Variant { kVarStd = 0, kVarSmall = 1, kVarCount = 2 };
 
 int variant_of(int nR, int nA, int bR, int bA, int lmax, int fb);
-// tc: network on the tensor cores in BF16 with FP32 accumulation (128 atoms per CTA).
-size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, bool tc);
-cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, bool tc, cudaStream_t st);
+// tcm: network products on the CUDA cores in FP32 (0), on the tensor cores
+// with BF16 operands and FP32 accumulation (1), or on the tensor cores with
+// split high/low BF16 operands, three products (2); 1 and 2 use 128 atoms per CTA.
+size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, int tcm);
+cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, int tcm, cudaStream_t st);
 
 // Per-structure FP64 reduction of per-atom contributions.  `max_atoms` is
 // the largest structure; `partial` holds n_pop * n_structs * reduce_chunks(max_atoms) * C doubles.
