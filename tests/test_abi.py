@@ -65,7 +65,8 @@ def test_create_validation(tn):
     bad.params = bad.params[:-1]
     assert _create_status(tn, [bad]) == 1
     assert _create_status(tn, [_desc(tn, l_max=6)]) in (1, 7)
-    assert _create_status(tn, [_desc(tn, mlp_precision=2)]) == 1
+    assert _create_status(tn, [_desc(tn, mlp_precision=3)]) == 1
+    assert _create_status(tn, [_desc(tn, mlp_precision=1, n_hidden=40)]) == 7
 
 
 def test_create_without_gpu_reports_no_device(tn):
