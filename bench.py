@@ -237,6 +237,49 @@ def population_bench(tn, synth, device, n_pop=50, gens=5):
             "candidates_ms": info["tune_ms"], "rmse_first": float(rmse[0])}
 
 
+def precision_report(tn, synth, device, n_frames=500, oracle_frames=1):
+    """BaZrO3 12x12x12 (8,640 atoms), 500 frames, rank-2 susceptibility:
+    the network on the CUDA cores in FP32 (mode 0), on the tensor cores in
+    BF16 (mode 1) and as split BF16 with three products (mode 2).  Errors per
+    tensor component: max over frames of |T_mode - T_0| / max_frames |T_0,c|,
+    and against the FP64 oracle on the first frame(s)."""
+    import torch
+    frames, types, box = synth.bzo_perovskite(n_frames=n_frames)
+    rng = np.random.default_rng(synth.seed_for(3, 1))
+    hp = synth.HyperParams(n_types=3, rank=2)
+    p = synth.model_params(hp, rng)
+    sc = synth.default_q_scaler(hp)
+    F = len(frames)
+    pos = torch.from_numpy(frames).to(torch.device("cuda", device))
+    bx = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(box, (F, 3)))).to(pos.device)
+    ty = torch.from_numpy(types).to(pos.device)
+    res, outs = {}, {}
+    for mode in (0, 1, 2):
+        ctx = tn.tnep_create([tn.Model.from_hyper(hp, p, sc, mode)], 3, RC, device=device)
+        tn.tnep_eval(ctx, pos, bx, ty)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (al,) = tn.tnep_eval(ctx, pos, bx, ty)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        outs[mode] = al.cpu().numpy()
+        res[mode] = {"atom_frames_per_s": F * len(types) / dt}
+        ctx.close()
+    scale = np.abs(outs[0]).max(0)
+    for mode in (1, 2):
+        d = np.abs(outs[mode] - outs[0]) / np.maximum(scale, 1e-30)
+        res[mode]["vs_fp32_max_rel_per_component"] = d.max(0).tolist()
+    import oracle
+    om = oracle.OracleModel.from_flat(hp, p, sc, *RC)
+    ref = np.array([oracle.evaluate(om, frames[f], box, types).tensor for f in range(oracle_frames)])
+    for mode in (0, 1, 2):
+        e = np.abs(outs[mode][:oracle_frames] - ref)
+        res[mode]["vs_fp64_rel_per_component"] = (e.max(0) / np.maximum(np.abs(ref).max(0), 1e-30)).tolist()
+        res[mode]["vs_fp64_rel_frobenius"] = float(np.linalg.norm(e) / np.linalg.norm(ref))
+    return {"workload": f"BaZrO3 12x12x12 (8,640 atoms), {F} frames, rank 2, 3 types",
+            "modes": {"fp32_cuda_cores": res[0], "bf16_tensor_cores": res[1], "split_bf16_tensor_cores": res[2]}}
+
+
 # ------------------------------------------------------------------ multi-rank
 def shard_seed_k(rank: int) -> int:
     """Each rank evaluates its own trajectory (weak scaling over frames):
@@ -303,6 +346,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-population", action="store_true")
     ap.add_argument("--mlp-precision", type=int, default=0)
+    ap.add_argument("--precision-report", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -424,6 +468,8 @@ def main():
                      "fused_launches_per_step": fused_launches / args.steps},
         "clocks": clocks,
     }
+    if rank == 0 and args.precision_report:
+        line["precision"] = precision_report(tn, synth, local)
     if rank == 0 and not args.no_population:
         line["population"] = population_bench(tn, synth, local)
     if rank == 0 and not args.no_serve:

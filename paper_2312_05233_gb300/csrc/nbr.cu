@@ -296,16 +296,49 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   int* wR = a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
   constexpr int ws = 32;
   int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
+  // Cell culling: squared distance from atom i to each stencil cell along
+  // each axis (0 for its own column); rows and x-cells that cannot hold a
+  // pair within the cutoff are skipped.  The test uses a cutoff enlarged by
+  // 1e-4 relative plus 1e-4 A, far above rounding, so it never drops a pair
+  // the float32 rule accepts.  (No culling on the per-pair rint path.)
+  float gx2[5], gy2[5], gz2[5];
+  {
+    const int cc[3] = {cx, cy, cz};
+    const float pc[3] = {pi.x, pi.y, pi.z};
+    float* g2[3] = {gx2, gy2, gz2};
+    const int* cl[3] = {xc, yc, zc};
+    const int na[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+      const float e = 1.0f / G.cinv[d];
+      const float xl = G.L[d] > 0.0f ? pc[d] : pc[d] - G.origin[d];
+      const float u = fminf(fmaxf(xl - (float)cc[d] * e, 0.0f), e);
+      for (int q = 0; q < na[d]; ++q) {
+        int o = cl[d][q] - cc[d];
+        if (G.L[d] > 0.0f) {  // relative offset of a wrapped cell
+          if (o > G.nc[d] / 2) o -= G.nc[d];
+          if (o < -(G.nc[d] / 2)) o += G.nc[d];
+        }
+        const float gap = use_rint ? 0.0f : (o > 0 ? (float)o * e - u : (o < 0 ? u + (float)(-o - 1) * e : 0.0f));
+        g2[d][q] = gap > 0.0f ? gap * gap : 0.0f;
+      }
+    }
+  }
+  const float rcm = a.rc_R * 1.0001f + 1e-4f;
+  const float rcm2 = rcm * rcm;
   int cR = 0, cA = 0;
   for (int iz = 0; iz < nz; ++iz) {
+    if (gz2[iz] >= rcm2) continue;
     for (int iy = 0; iy < ny; ++iy) {
+      const float rem = rcm2 - gz2[iz] - gy2[iy];
+      if (rem <= 0.0f) continue;
       const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
       const float sy = ys[iy], sz = zs[iz];
       int ix = 0;
       while (ix < nx) {
-        // merge x-cells that are contiguous and share a shift into one range
+        if (gx2[ix] >= rem) { ++ix; continue; }
+        // merge x-cells that are contiguous, share a shift and survive culling
         int ie = ix + 1;
-        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) ++ie;
+        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix] && gx2[ie] < rem) ++ie;
         const float sx = xs[ix];
         const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
         ix = ie;

@@ -89,65 +89,45 @@ __device__ __forceinline__ void real_harmonics(float x, float y, float z, float*
 }
 
 // V += sum_lm S_lm * grad p_lm(x, y, z)  (gradient of the polynomial as written).
+// Each order l accumulates into its own partial sums so that the four
+// dependency chains run side by side.
 template <int LMAX>
 __device__ __forceinline__ void harmonic_grad(const float* S, float x, float y, float z, float& vx, float& vy,
                                               float& vz) {
-  vx += S[0]; vy += S[1]; vz += S[2];
+  float ax = S[0], ay = S[1], az = S[2];
+  float bx = 0.f, by = 0.f, bz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
   if constexpr (LMAX >= 2) {
-    vx += y * S[3] + z * S[5] + 2.f * x * S[6];
-    vy += x * S[3] + z * S[4] - 2.f * y * S[6];
-    vz += y * S[4] + x * S[5] + 6.f * z * S[7];
+    bx = y * S[3] + z * S[5] + 2.f * x * S[6];
+    by = x * S[3] + z * S[4] - 2.f * y * S[6];
+    bz = y * S[4] + x * S[5] + 6.f * z * S[7];
     if constexpr (LMAX >= 3) {
       const float x2 = x * x, y2 = y * y, z2 = z * z;
       const float xy = x * y, yz = y * z, xz = x * z;
       const float t5 = 5.f * z2 - 1.f;
-      // p8 = 3x^2y - y^3
-      vx += 6.f * xy * S[8];
-      vy += (3.f * x2 - 3.f * y2) * S[8];
-      // p9 = xyz
-      vx += yz * S[9]; vy += xz * S[9]; vz += xy * S[9];
-      // p10 = y(5z^2-1)
-      vy += t5 * S[10]; vz += 10.f * yz * S[10];
-      // p11 = 5z^3 - 3z
-      vz += (15.f * z2 - 3.f) * S[11];
-      // p12 = x(5z^2-1)
-      vx += t5 * S[12]; vz += 10.f * xz * S[12];
-      // p13 = z(x^2-y^2)
-      vx += 2.f * xz * S[13]; vy -= 2.f * yz * S[13]; vz += (x2 - y2) * S[13];
-      // p14 = x^3 - 3xy^2
-      vx += (3.f * x2 - 3.f * y2) * S[14]; vy -= 6.f * xy * S[14];
+      // p8 = 3x^2y - y^3, p9 = xyz, p10 = y(5z^2-1), p11 = 5z^3 - 3z,
+      // p12 = x(5z^2-1), p13 = z(x^2-y^2), p14 = x^3 - 3xy^2
+      cx = 6.f * xy * S[8] + yz * S[9] + t5 * S[12] + 2.f * xz * S[13] + (3.f * x2 - 3.f * y2) * S[14];
+      cy = (3.f * x2 - 3.f * y2) * S[8] + xz * S[9] + t5 * S[10] - 2.f * yz * S[13] - 6.f * xy * S[14];
+      cz = xy * S[9] + 10.f * yz * S[10] + (15.f * z2 - 3.f) * S[11] + 10.f * xz * S[12] + (x2 - y2) * S[13];
       if constexpr (LMAX >= 4) {
-        const float t7 = 7.f * z2 - 1.f;
+        const float t7 = 7.f * z2 - 1.f, t73 = 7.f * z2 - 3.f;
         const float xyz = xy * z;
-        // p15 = x^3 y - x y^3
-        vx += (3.f * x2 * y - y2 * y) * S[15];
-        vy += (x2 * x - 3.f * x * y2) * S[15];
-        // p16 = 3x^2yz - y^3 z
-        vx += 6.f * xyz * S[16];
-        vy += (3.f * x2 - 3.f * y2) * z * S[16];
-        vz += (3.f * x2 * y - y2 * y) * S[16];
-        // p17 = xy(7z^2-1)
-        vx += y * t7 * S[17]; vy += x * t7 * S[17]; vz += 14.f * xyz * S[17];
-        // p18 = 7yz^3 - 3yz
-        vy += (7.f * z2 - 3.f) * z * S[18];
-        vz += (21.f * z2 - 3.f) * y * S[18];
-        // p19 = 35z^4 - 30z^2 + 3
-        vz += (140.f * z2 - 60.f) * z * S[19];
-        // p20 = xz(7z^2-3)
-        vx += (7.f * z2 - 3.f) * z * S[20];
-        vz += (21.f * z2 - 3.f) * x * S[20];
-        // p21 = (x^2-y^2)(7z^2-1)
-        vx += 2.f * x * t7 * S[21]; vy -= 2.f * y * t7 * S[21]; vz += 14.f * z * (x2 - y2) * S[21];
-        // p22 = x^3 z - 3 x y^2 z
-        vx += (3.f * x2 - 3.f * y2) * z * S[22];
-        vy -= 6.f * xyz * S[22];
-        vz += (x2 * x - 3.f * x * y2) * S[22];
-        // p23 = x^4 - 6x^2y^2 + y^4
-        vx += (4.f * x2 * x - 12.f * x * y2) * S[23];
-        vy += (4.f * y2 * y - 12.f * x2 * y) * S[23];
+        // p15 = x^3 y - x y^3, p16 = 3x^2yz - y^3 z, p17 = xy(7z^2-1),
+        // p18 = 7yz^3 - 3yz, p19 = 35z^4 - 30z^2 + 3, p20 = xz(7z^2-3),
+        // p21 = (x^2-y^2)(7z^2-1), p22 = x^3 z - 3 x y^2 z, p23 = x^4 - 6x^2y^2 + y^4
+        dx = (3.f * x2 * y - y2 * y) * S[15] + 6.f * xyz * S[16] + y * t7 * S[17] + t73 * z * S[20] +
+             2.f * x * t7 * S[21] + (3.f * x2 - 3.f * y2) * z * S[22] + (4.f * x2 * x - 12.f * x * y2) * S[23];
+        dy = (x2 * x - 3.f * x * y2) * S[15] + (3.f * x2 - 3.f * y2) * z * S[16] + x * t7 * S[17] +
+             t73 * z * S[18] - 2.f * y * t7 * S[21] - 6.f * xyz * S[22] + (4.f * y2 * y - 12.f * x2 * y) * S[23];
+        dz = (3.f * x2 * y - y2 * y) * S[16] + 14.f * xyz * S[17] + (21.f * z2 - 3.f) * y * S[18] +
+             (140.f * z2 - 60.f) * z * S[19] + (21.f * z2 - 3.f) * x * S[20] + 14.f * z * (x2 - y2) * S[21] +
+             (x2 * x - 3.f * x * y2) * S[22];
       }
     }
   }
+  vx += (ax + bx) + (cx + dx);
+  vy += (ay + by) + (cy + dy);
+  vz += (az + bz) + (cz + dz);
 }
 
 // Loads one (t_i, t_j) coefficient block c[n][k] from shared memory.
@@ -547,15 +527,16 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       float p[NLM];
       real_harmonics<LMAX>(ux, uy, uz, p);
       float S[NLM];
-      float srad = 0.f;
+      float sr[4] = {0.f, 0.f, 0.f, 0.f};  // per-order partial sums of sum_lm T_lm p_lm
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) {
         float sv = 0.f, tv = 0.f;
 #pragma unroll
         for (int n = 0; n < NA; ++n) { sv += G[n * NLM + lm] * g[n]; tv += G[n * NLM + lm] * dg[n]; }
         S[lm] = sv;
-        srad += tv * p[lm];
+        sr[l_of(lm) - 1] += tv * p[lm];
       }
+      const float srad = (sr[0] + sr[1]) + (sr[2] + sr[3]);
       float vx = 0.f, vy = 0.f, vz = 0.f;
       harmonic_grad<LMAX>(S, ux, uy, uz, vx, vy, vz);
       const float uv = ux * vx + uy * vy + uz * vz;
