@@ -257,6 +257,30 @@ __device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* 
   return n;
 }
 
+// Appends one atom's list entries four at a time: entries 4g..4g+3 of atom i
+// are contiguous in the quad-interleaved layout, so each flush is one 16-byte
+// store instead of four scattered 4-byte ones.  Entries past the capacity are
+// counted but not stored; slots past the count in the last group hold junk
+// that readers never look at.
+struct QuadWriter {
+  int* list;
+  int i, cap, n;
+  int b0, b1, b2, b3;
+  __device__ __forceinline__ QuadWriter(int* l, int i_, int cap_) : list(l), i(i_), cap(cap_), n(0), b0(0), b1(0), b2(0), b3(0) {}
+  __device__ __forceinline__ void push(int v) {
+    const int q = n & 3;
+    b0 = q == 0 ? v : b0;
+    b1 = q == 1 ? v : b1;
+    b2 = q == 2 ? v : b2;
+    b3 = q == 3 ? v : b3;
+    ++n;
+    if (q == 3 && n <= cap) *reinterpret_cast<int4*>(list + nbr_index(i, n - 4, cap)) = make_int4(b0, b1, b2, b3);
+  }
+  __device__ __forceinline__ void flush() {
+    if ((n & 3) != 0 && n <= cap) *reinterpret_cast<int4*>(list + nbr_index(i, n & ~3, cap)) = make_int4(b0, b1, b2, b3);
+  }
+};
+
 // Minimum-image difference with every operation rounded separately.
 __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
   float d = __fsub_rn(xj, xi);
@@ -292,53 +316,16 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   // give the float32 rule of the header bit for bit.
   const bool use_rint = nx < 0 || ny < 0 || nz < 0 || (a.struct_flags[s] & 1);
   nx = abs(nx); ny = abs(ny); nz = abs(nz);
-  // scratch entry e of this thread lives at wR[e * ws]
-  int* wR = a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
-  constexpr int ws = 32;
-  int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
-  // Cell culling: squared distance from atom i to each stencil cell along
-  // each axis (0 for its own column); rows and x-cells that cannot hold a
-  // pair within the cutoff are skipped.  The test uses a cutoff enlarged by
-  // 1e-4 relative plus 1e-4 A, far above rounding, so it never drops a pair
-  // the float32 rule accepts.  (No culling on the per-pair rint path.)
-  float gx2[5], gy2[5], gz2[5];
-  {
-    const int cc[3] = {cx, cy, cz};
-    const float pc[3] = {pi.x, pi.y, pi.z};
-    float* g2[3] = {gx2, gy2, gz2};
-    const int* cl[3] = {xc, yc, zc};
-    const int na[3] = {nx, ny, nz};
-    for (int d = 0; d < 3; ++d) {
-      const float e = 1.0f / G.cinv[d];
-      const float xl = G.L[d] > 0.0f ? pc[d] : pc[d] - G.origin[d];
-      const float u = fminf(fmaxf(xl - (float)cc[d] * e, 0.0f), e);
-      for (int q = 0; q < na[d]; ++q) {
-        int o = cl[d][q] - cc[d];
-        if (G.L[d] > 0.0f) {  // relative offset of a wrapped cell
-          if (o > G.nc[d] / 2) o -= G.nc[d];
-          if (o < -(G.nc[d] / 2)) o += G.nc[d];
-        }
-        const float gap = use_rint ? 0.0f : (o > 0 ? (float)o * e - u : (o < 0 ? u + (float)(-o - 1) * e : 0.0f));
-        g2[d][q] = gap > 0.0f ? gap * gap : 0.0f;
-      }
-    }
-  }
-  const float rcm = a.rc_R * 1.0001f + 1e-4f;
-  const float rcm2 = rcm * rcm;
-  int cR = 0, cA = 0;
+  QuadWriter qR(a.nbr_tmp, i, a.cap_R), qA(a.nbr_A, i, a.cap_A);
   for (int iz = 0; iz < nz; ++iz) {
-    if (gz2[iz] >= rcm2) continue;
     for (int iy = 0; iy < ny; ++iy) {
-      const float rem = rcm2 - gz2[iz] - gy2[iy];
-      if (rem <= 0.0f) continue;
       const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
       const float sy = ys[iy], sz = zs[iz];
       int ix = 0;
       while (ix < nx) {
-        if (gx2[ix] >= rem) { ++ix; continue; }
-        // merge x-cells that are contiguous, share a shift and survive culling
+        // merge x-cells that are contiguous and share a shift into one range
         int ie = ix + 1;
-        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix] && gx2[ie] < rem) ++ie;
+        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) ++ie;
         const float sx = xs[ix];
         const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
         ix = ie;
@@ -373,61 +360,45 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
           while (mR) {
             const int j = jb + __ffs(mR) - 1;
             mR &= mR - 1;
-            if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
-            ++cR;
+            qR.push(j | (__float_as_int(a.pos4[j].w) << kTypeShift));
           }
           while (mA) {
             const int j = jb + __ffs(mA) - 1;
             mA &= mA - 1;
-            if (cA < a.cap_A) wA[(size_t)cA * 32] = j;
-            ++cA;
+            qA.push(j);
           }
         }
       }
     }
   }
+  qR.flush();
+  qA.flush();
+  const int cR = qR.n, cA = qA.n;
   a.cnt_R[i] = cR;
   a.cnt_A[i] = cA;
   if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
   if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
-  // counting sort of the radial entries by neighbour type; the scratch rows
-  // are read eight at a time so that eight loads are in flight per warp
+  // stable partition of the radial entries by neighbour type: one pass over
+  // the scratch (read in 16-byte groups) per type, written in 16-byte groups
   const int n = min(cR, a.cap_R);
   int cnt[kMaxTypes];
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u) cnt[u] = 0;
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    int v[8];
+  QuadWriter qo(a.nbr_R, i, a.cap_R);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = (e0 + q < n) ? wR[(size_t)(e0 + q) * ws] : 0;
+  for (int u = 0; u < kMaxTypes; ++u) {
+    if (u >= a.n_types) break;
+    const int before = qo.n;
+    for (int e0 = 0; e0 < n; e0 += 4) {
+      const int4 v = *reinterpret_cast<const int4*>(a.nbr_tmp + nbr_index(i, e0, a.cap_R));
+      const int vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int t = (e0 + q < n) ? (int)((unsigned)v[q] >> kTypeShift) : -1;
-#pragma unroll
-      for (int u = 0; u < kMaxTypes; ++u) cnt[u] += (t == u);
+      for (int q = 0; q < 4; ++q)
+        if (e0 + q < n && (int)((unsigned)vv[q] >> kTypeShift) == u) qo.push(vv[q] & kIndexMask);
     }
+    cnt[u] = qo.n - before;
   }
-  int off[kMaxTypes];
-  int run = 0;
-#pragma unroll
-  for (int u = 0; u < kMaxTypes; ++u) { off[u] = run; run += cnt[u]; }
-  int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    int v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = (e0 + q < n) ? wR[(size_t)(e0 + q) * ws] : 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (e0 + q < n) {
-        const int t = (unsigned)v[q] >> kTypeShift;
-        int dst = 0;
-#pragma unroll
-        for (int u = 0; u < kMaxTypes; ++u)
-          if (t == u) { dst = off[u]; off[u] = dst + 1; }
-        outR[(size_t)dst * 32] = v[q] & kIndexMask;
-      }
-    }
-  }
+  qo.flush();
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u)
     if (u < a.n_types) a.seg_R[(size_t)u * a.seg_stride + i] = cnt[u];
