@@ -257,30 +257,6 @@ __device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* 
   return n;
 }
 
-// Appends one atom's list entries four at a time: entries 4g..4g+3 of atom i
-// are contiguous in the quad-interleaved layout, so each flush is one 16-byte
-// store instead of four scattered 4-byte ones.  Entries past the capacity are
-// counted but not stored; slots past the count in the last group hold junk
-// that readers never look at.
-struct QuadWriter {
-  int* list;
-  int i, cap, n;
-  int b0, b1, b2, b3;
-  __device__ __forceinline__ QuadWriter(int* l, int i_, int cap_) : list(l), i(i_), cap(cap_), n(0), b0(0), b1(0), b2(0), b3(0) {}
-  __device__ __forceinline__ void push(int v) {
-    const int q = n & 3;
-    b0 = q == 0 ? v : b0;
-    b1 = q == 1 ? v : b1;
-    b2 = q == 2 ? v : b2;
-    b3 = q == 3 ? v : b3;
-    ++n;
-    if (q == 3 && n <= cap) *reinterpret_cast<int4*>(list + nbr_index(i, n - 4, cap)) = make_int4(b0, b1, b2, b3);
-  }
-  __device__ __forceinline__ void flush() {
-    if ((n & 3) != 0 && n <= cap) *reinterpret_cast<int4*>(list + nbr_index(i, n & ~3, cap)) = make_int4(b0, b1, b2, b3);
-  }
-};
-
 // Minimum-image difference with every operation rounded separately.
 __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
   float d = __fsub_rn(xj, xi);
@@ -316,7 +292,11 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   // give the float32 rule of the header bit for bit.
   const bool use_rint = nx < 0 || ny < 0 || nz < 0 || (a.struct_flags[s] & 1);
   nx = abs(nx); ny = abs(ny); nz = abs(nz);
-  QuadWriter qR(a.nbr_tmp, i, a.cap_R), qA(a.nbr_A, i, a.cap_A);
+  // scratch entry e of this thread lives at wR[e * ws]
+  int* wR = a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
+  constexpr int ws = 32;
+  int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
+  int cR = 0, cA = 0;
   for (int iz = 0; iz < nz; ++iz) {
     for (int iy = 0; iy < ny; ++iy) {
       const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
@@ -360,45 +340,61 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
           while (mR) {
             const int j = jb + __ffs(mR) - 1;
             mR &= mR - 1;
-            qR.push(j | (__float_as_int(a.pos4[j].w) << kTypeShift));
+            if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
+            ++cR;
           }
           while (mA) {
             const int j = jb + __ffs(mA) - 1;
             mA &= mA - 1;
-            qA.push(j);
+            if (cA < a.cap_A) wA[(size_t)cA * 32] = j;
+            ++cA;
           }
         }
       }
     }
   }
-  qR.flush();
-  qA.flush();
-  const int cR = qR.n, cA = qA.n;
   a.cnt_R[i] = cR;
   a.cnt_A[i] = cA;
   if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
   if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
-  // stable partition of the radial entries by neighbour type: one pass over
-  // the scratch (read in 16-byte groups) per type, written in 16-byte groups
+  // counting sort of the radial entries by neighbour type; the scratch rows
+  // are read eight at a time so that eight loads are in flight per warp
   const int n = min(cR, a.cap_R);
   int cnt[kMaxTypes];
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u) cnt[u] = 0;
-  QuadWriter qo(a.nbr_R, i, a.cap_R);
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    int v[8];
 #pragma unroll
-  for (int u = 0; u < kMaxTypes; ++u) {
-    if (u >= a.n_types) break;
-    const int before = qo.n;
-    for (int e0 = 0; e0 < n; e0 += 4) {
-      const int4 v = *reinterpret_cast<const int4*>(a.nbr_tmp + nbr_index(i, e0, a.cap_R));
-      const int vv[4] = {v.x, v.y, v.z, v.w};
+    for (int q = 0; q < 8; ++q) v[q] = (e0 + q < n) ? wR[(size_t)(e0 + q) * ws] : 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (e0 + q < n && (int)((unsigned)vv[q] >> kTypeShift) == u) qo.push(vv[q] & kIndexMask);
+    for (int q = 0; q < 8; ++q) {
+      const int t = (e0 + q < n) ? (int)((unsigned)v[q] >> kTypeShift) : -1;
+#pragma unroll
+      for (int u = 0; u < kMaxTypes; ++u) cnt[u] += (t == u);
     }
-    cnt[u] = qo.n - before;
   }
-  qo.flush();
+  int off[kMaxTypes];
+  int run = 0;
+#pragma unroll
+  for (int u = 0; u < kMaxTypes; ++u) { off[u] = run; run += cnt[u]; }
+  int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    int v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (e0 + q < n) ? wR[(size_t)(e0 + q) * ws] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (e0 + q < n) {
+        const int t = (unsigned)v[q] >> kTypeShift;
+        int dst = 0;
+#pragma unroll
+        for (int u = 0; u < kMaxTypes; ++u)
+          if (t == u) { dst = off[u]; off[u] = dst + 1; }
+        outR[(size_t)dst * 32] = v[q] & kIndexMask;
+      }
+    }
+  }
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u)
     if (u < a.n_types) a.seg_R[(size_t)u * a.seg_stride + i] = cnt[u];

@@ -41,14 +41,11 @@ struct StructBox {
   float invL[3];
 };
 
-// Neighbour lists are stored warp-tiled in groups of four: entries
-// 4g..4g+3 of atom i are 16 contiguous bytes at int offset
-// ((i >> 5) * (cap / 4) + g) * 128 + (i & 31) * 4, so the 32 atoms of a warp
-// keep their lists in one contiguous tile, each 512-byte row of the tile
-// holds four entries of every atom, and writers can store 16 bytes at a time.
-// Capacities are multiples of 4.
+// Neighbour lists are stored warp-tiled: entry k of atom i lives at
+// ((i >> 5) * cap + k) * 32 + (i & 31), so one warp's lists are contiguous
+// and every row of 32 entries is one 128-byte line.
 __host__ __device__ __forceinline__ size_t nbr_index(int i, int k, int cap) {
-  return ((size_t)(i >> 5) * (cap >> 2) + (k >> 2)) * 128 + (i & 31) * 4 + (k & 3);
+  return ((size_t)(i >> 5) * cap + k) * 32 + (i & 31);
 }
 
 // Arguments of the neighbour-list pipeline.
