@@ -347,6 +347,7 @@ def main():
     ap.add_argument("--no-population", action="store_true")
     ap.add_argument("--mlp-precision", type=int, default=0)
     ap.add_argument("--precision-report", action="store_true")
+    ap.add_argument("--skin", type=float, default=0.5, help="Verlet skin of the extra skin-reuse measurement")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -439,6 +440,26 @@ def main():
     barrier()
     e2e_ms = max_over_ranks(dist, (time.perf_counter() - t0) * 1e3 / args.steps, dev, world)
 
+    # the same trajectory with Verlet-skin list reuse (every frame still uses
+    # exactly the pairs within the cutoffs; reported beside the headline,
+    # which rebuilds the lists for every frame)
+    skin_line = None
+    if args.skin > 0:
+        tn.tnep_set_option(ctx, tn.TNEP_OPT_SKIN, args.skin)
+        step_device()
+        barrier()
+        es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+        es1.record(stream)
+        barrier()
+        sk_ms = max_over_ranks(dist, es0.elapsed_time(es1) / args.steps, dev, world)
+        skin_line = {"skin_A": args.skin, "value": job_units(F, N, world) / (sk_ms * 1e-3), "ms_per_step": sk_ms,
+                     "lists_reused_every_pass": bool(tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_SKIN_USED)),
+                     "nbr_ms_per_step": tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_NBR_MS)}
+        tn.tnep_set_option(ctx, tn.TNEP_OPT_SKIN, 0.0)
+
     # neighbour statistics of the last frame for the flop model
     offs = np.array([0, N])
     cR, cA, _, _ = tn.tnep_neighbors(ctx, offs, frames[-1], box[None], cap_R=1, cap_A=1)
@@ -467,6 +488,7 @@ def main():
                      "fused_ms_per_step": fused_ms / args.steps, "nbr_ms_per_step": nbr_ms / args.steps,
                      "fused_launches_per_step": fused_launches / args.steps},
         "clocks": clocks,
+        "skin_reuse": skin_line,
     }
     if rank == 0 and args.precision_report:
         line["precision"] = precision_report(tn, synth, local)

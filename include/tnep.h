@@ -283,7 +283,15 @@ enum {
   TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2} (default 1) */
   TNEP_OPT_LAST_KERNEL_LAUNCHES = 5,/* read-only: fused-kernel launches in the last call */
   TNEP_OPT_LAST_NBR_MS = 6,         /* read-only: device time of the cell/neighbour pipeline in the last call (ms) */
-  TNEP_OPT_KERNEL_LAUNCHES_TOTAL = 7 /* read-only: kernels launched by this library in this process */
+  TNEP_OPT_KERNEL_LAUNCHES_TOTAL = 7,/* read-only: kernels launched by this library in this process */
+  TNEP_OPT_SKIN = 8,                /* Verlet skin (A) for tnep_eval, default 0.  With a skin s > 0 each pass of
+                                       frames builds lists with cutoffs + s for its first frame and re-tests those
+                                       candidates under each frame's positions with the exact float32 pair rule,
+                                       so every frame still sees exactly the pairs within the cutoffs; if an atom
+                                       moved more than s / 2 within a pass, or the box changed, the call redoes
+                                       every pass with lists built per frame.  Results agree with s = 0 to float32
+                                       rounding (pair order may differ). */
+  TNEP_OPT_LAST_SKIN_USED = 9       /* read-only: 1 if the last tnep_eval used skin lists in every pass */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

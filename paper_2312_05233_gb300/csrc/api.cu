@@ -66,6 +66,8 @@ tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_k1);
   if (e == cudaSuccess) e = cudaMalloc(&c->ws.d_status, sizeof(DevStatus));
   if (e == cudaSuccess) e = c->ws.h_status.ensure(1);
+  if (e == cudaSuccess) e = cudaMalloc(&c->skin_ws.d_status, sizeof(DevStatus));
+  if (e == cudaSuccess) e = c->skin_ws.h_status.ensure(1);
   if (e != cudaSuccess) return bail(cuda_fail(e, "context setup"));
   for (int k = 0; k < n_models; ++k) {
     Model m;
@@ -107,6 +109,7 @@ void tnep_destroy(tnep_ctx* c) {
   for (auto& m : c->models)
     if (m.d_packed) cudaFree(m.d_packed);
   c->ws.release();
+  c->skin_ws.release();
   c->pop_params.release();
   c->pop_target.release();
   c->pop_rmse.release();
@@ -149,6 +152,10 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       if (value != 1 && value != 2) return fail(TNEP_ERR_INVALID, "cell subdivision must be 1 or 2");
       c->cell_div = (int)value;
       return TNEP_OK;
+    case TNEP_OPT_SKIN:
+      if (!(value >= 0.0) || value > 2.0) return fail(TNEP_ERR_INVALID, "skin must be in [0, 2] Angstrom");
+      c->skin = (float)value;
+      return TNEP_OK;
     default:
       return fail(TNEP_ERR_INVALID, "unknown or read-only option");
   }
@@ -165,6 +172,8 @@ tnep_status tnep_get_option(const tnep_ctx* c, int option, double* value) {
     case TNEP_OPT_LAST_KERNEL_LAUNCHES: *value = c->last_launches; return TNEP_OK;
     case TNEP_OPT_LAST_NBR_MS: *value = c->last_nbr_ms; return TNEP_OK;
     case TNEP_OPT_KERNEL_LAUNCHES_TOTAL: *value = (double)launches_total(); return TNEP_OK;
+    case TNEP_OPT_SKIN: *value = c->skin; return TNEP_OK;
+    case TNEP_OPT_LAST_SKIN_USED: *value = c->last_skin_used; return TNEP_OK;
     default: return fail(TNEP_ERR_INVALID, "unknown option");
   }
 }
@@ -197,8 +206,14 @@ tnep_status tnep_eval(tnep_ctx* c, int n_frames, int n_atoms, const float* pos, 
   if (box) TNEP_TRY(stage_in(box, (size_t)3 * n_frames, c->ws.box_stage, &d_box_all, st));
   if (!out_dev) TNEP_CUDA(c->h_out.ensure((size_t)n_frames * Ctot));
   std::vector<int> offs(fb + 1);
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  // Verlet-skin reuse needs one box for the whole pass and n_atoms > 0; any
+  // violation found on the device (displacement above skin / 2, changed box,
+  // box too small for the enlarged cutoff) redoes the call with fresh lists
+  // for every frame.
+  bool use_skin = c->skin > 0.f && n_atoms > 0;
+  for (int attempt = 0; attempt < 6; ++attempt) {
     TNEP_TRY(reset_status(c->ws, st));
+    if (use_skin) TNEP_TRY(reset_status(c->skin_ws, st));
     int n_pass = 0;
     for (int f0 = 0, b = 0; f0 < n_frames; f0 += fb, ++b) {
       cudaEvent_t* ev = nullptr;
@@ -220,7 +235,10 @@ tnep_status tnep_eval(tnep_ctx* c, int n_frames, int n_atoms, const float* pos, 
       }
       const float* d_box = d_box_all ? d_box_all + (size_t)3 * f0 : nullptr;
       TNEP_CUDA(cudaEventRecord(ev[0], st));
-      TNEP_TRY(build_lists(c, c->ws, st, nf, offs.data(), d_pos, d_box, d_types, n_atoms));
+      if (use_skin)
+        TNEP_TRY(skin_lists(c, c->ws, c->skin_ws, st, nf, n_atoms, d_pos, d_box, d_types));
+      else
+        TNEP_TRY(build_lists(c, c->ws, st, nf, offs.data(), d_pos, d_box, d_types, n_atoms));
       if (!pos_dev && n_atoms > 0) TNEP_CUDA(cudaEventRecord(c->ev_consumed[b & 1], st));
       TNEP_CUDA(cudaEventRecord(ev[1], st));
       TNEP_TRY(run_models(c, c->ws, st, nf, nf * n_atoms, ev[2]));
@@ -233,10 +251,30 @@ tnep_status tnep_eval(tnep_ctx* c, int n_frames, int n_atoms, const float* pos, 
         dst_base += (size_t)n_frames * m.C;
       }
     }
+    if (use_skin) {
+      TNEP_CUDA(cudaMemcpyAsync(c->skin_ws.h_status.p, c->skin_ws.d_status, sizeof(DevStatus),
+                                cudaMemcpyDeviceToHost, st));
+      TNEP_CUDA(cudaStreamSynchronize(st));
+      const DevStatus sk = *c->skin_ws.h_status.p;
+      if (sk.error) {  // e.g. a box shorter than 2 (rc + skin): plain lists instead
+        use_skin = false;
+        continue;
+      }
+      if (sk.max_cnt_R > c->skin_cap) {
+        c->skin_cap = round_up(sk.max_cnt_R + 16, 32);
+        if (c->skin_cap > c->max_neighbors) use_skin = false;
+        continue;
+      }
+    }
     bool regrow = false;
     TNEP_TRY(finish(c, c->ws, st, &regrow));
     TNEP_TRY(sum_pass_times(c, n_pass));
+    if (use_skin && c->ws.h_status.p->skin_violation) {
+      use_skin = false;
+      continue;
+    }
     if (!regrow) {
+      c->last_skin_used = use_skin ? 1 : 0;
       if (!out_dev) std::memcpy(out, c->h_out.p, sizeof(double) * (size_t)n_frames * Ctot);
       return TNEP_OK;
     }

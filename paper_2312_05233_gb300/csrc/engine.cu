@@ -117,8 +117,8 @@ tnep_status validate_model(const tnep_model_desc& d, int T) {
 }
 
 // Builds cell and neighbour lists for a batch whose inputs are on the device.
-tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const int* h_offsets, const float* d_pos,
-                        const float* d_box, const int* d_types, int types_period) {
+tnep_status ensure_batch(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const int* h_offsets, int cap_R,
+                         int cap_A) {
   const int N = h_offsets[S];
   const int stride = round_up(std::max(N, 1), 32);
   int mx = 0;
@@ -126,8 +126,8 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   w.max_atoms = mx;
   w.atom_stride = stride;
   w.cells_cap = 2 * N + 8 * S;
-  w.cap_R = c->cap_R;
-  w.cap_A = c->cap_A;
+  w.cap_R = cap_R;
+  w.cap_A = cap_A;
   TNEP_CUDA(w.offsets.ensure(S + 1));
   TNEP_CUDA(w.struct_cells.ensure(S + 1));
   TNEP_CUDA(w.struct_flags.ensure(S));
@@ -150,6 +150,14 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   TNEP_CUDA(w.nbr_A.ensure((size_t)stride * w.cap_A));
   TNEP_CUDA(w.seg_R.ensure((size_t)stride * c->n_types));
   TNEP_CUDA(cudaMemcpyAsync(w.offsets.p, h_offsets, sizeof(int) * (S + 1), cudaMemcpyHostToDevice, st));
+  return TNEP_OK;
+}
+
+tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const int* h_offsets, const float* d_pos,
+                        const float* d_box, const int* d_types, int types_period, const ListSpec* spec) {
+  const float rc_R = spec ? spec->rc_R : c->rc_R, rc_A = spec ? spec->rc_A : c->rc_A;
+  TNEP_TRY(ensure_batch(c, w, st, S, h_offsets, spec ? spec->cap_R : c->cap_R, spec ? spec->cap_A : c->cap_A));
+  const int N = h_offsets[S];
   TNEP_CUDA(cudaMemsetAsync(w.cell_count.p, 0, sizeof(int) * (w.cells_cap + 1), st));
   TNEP_CUDA(cudaMemsetAsync(w.struct_flags.p, 0, sizeof(int) * S, st));
   NbrArgs a{};
@@ -161,8 +169,8 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   a.types = d_types;
   a.types_period = std::max(types_period, 1);
   a.n_types = c->n_types;
-  a.rc_R = c->rc_R;
-  a.rc_A = c->rc_A;
+  a.rc_R = rc_R;
+  a.rc_A = rc_A;
   a.cell_div = c->cell_div;
   a.grids = w.grids.p;
   a.boxes = w.boxes.p;
@@ -182,7 +190,7 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   a.nbr_A = w.nbr_A.p;
   a.nbr_tmp = w.nbr_tmp.p;
   a.seg_R = w.seg_R.p;
-  a.seg_stride = stride;
+  a.seg_stride = w.atom_stride;
   a.cnt_R = w.cnt_R.p;
   a.cnt_A = w.cnt_A.p;
   a.cap_R = w.cap_R;
@@ -190,6 +198,53 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   a.cells_cap = w.cells_cap;
   a.status = w.d_status;
   TNEP_CUDA(launch_neighbor_pipeline(a, st));
+  return TNEP_OK;
+}
+
+// Trajectory pass with Verlet-skin reuse: skin lists (cutoffs + skin) of the
+// pass's first frame in `sw`, then every frame's exact lists compacted from
+// them into `w` (frames in the first frame's cell order).  Raises
+// skin_violation in w's status when an atom moved more than skin / 2.
+tnep_status skin_lists(tnep_ctx* c, Workspace& w, Workspace& sw, cudaStream_t st, int nf, int N, const float* d_pos,
+                       const float* d_box, const int* d_types) {
+  const int one[2] = {0, N};
+  ListSpec spec{c->rc_R + c->skin, c->rc_A + c->skin, c->skin_cap, 4};
+  TNEP_TRY(build_lists(c, sw, st, 1, one, d_pos, d_box, d_types, N, &spec));
+  std::vector<int> offs(nf + 1);
+  for (int k = 0; k <= nf; ++k) offs[k] = k * N;
+  TNEP_TRY(ensure_batch(c, w, st, nf, offs.data(), c->cap_R, c->cap_A));
+  SkinArgs a{};
+  a.nf = nf;
+  a.N = N;
+  a.pos = d_pos;
+  a.box = d_box;
+  a.types = d_types;
+  a.types_period = std::max(N, 1);
+  a.n_types = c->n_types;
+  a.sorted_orig = sw.sorted_orig.p;
+  a.ref4 = sw.pos4.p;
+  a.ref_box = sw.boxes.p;
+  a.skin_nbr = sw.nbr_R.p;
+  a.skin_seg = sw.seg_R.p;
+  a.skin_cap = sw.cap_R;
+  a.skin_seg_stride = sw.atom_stride;
+  a.rc2R = c->rc_R * c->rc_R;
+  a.rc2A = c->rc_A * c->rc_A;
+  const float hs = 0.5f * c->skin * 0.999f;
+  a.half_skin2 = hs * hs;
+  a.pos4 = w.pos4.p;
+  a.sorted_struct = w.sorted_struct.p;
+  a.boxes = w.boxes.p;
+  a.nbr_R = w.nbr_R.p;
+  a.nbr_A = w.nbr_A.p;
+  a.cnt_R = w.cnt_R.p;
+  a.cnt_A = w.cnt_A.p;
+  a.seg_R = w.seg_R.p;
+  a.seg_stride = w.atom_stride;
+  a.cap_R = w.cap_R;
+  a.cap_A = w.cap_A;
+  a.status = w.d_status;
+  TNEP_CUDA(launch_skin_compact(a, st));
   return TNEP_OK;
 }
 

@@ -146,6 +146,10 @@ struct tnep_ctx {
   int max_neighbors = 1024;
   int frames_per_batch = 0;
   int cell_div = 1;
+  float skin = 0.f;        // Verlet skin for trajectories (0 = lists rebuilt every frame)
+  int skin_cap = 160;      // radial capacity of the skin lists
+  Workspace skin_ws;       // skin lists of the current pass's first frame
+  int last_skin_used = 0;  // the last tnep_eval reused skin lists in every pass
   int block_atoms = 128;  // atoms per CTA of the fused kernel (64 or 128)
   double last_kernel_ms = 0.0;
   double last_nbr_ms = 0.0;
@@ -159,8 +163,17 @@ tnep_status pack_model(tnep_ctx* c, Model& m);
 void pack_params(const Model& m, int T, const float* flat, const float* scaler, float* out);
 size_t expected_params(const tnep_model_desc& d, int T);
 tnep_status validate_model(const tnep_model_desc& d, int T);
+// Cutoffs and capacities of one list build (default: the context's).
+struct ListSpec {
+  float rc_R, rc_A;
+  int cap_R, cap_A;
+};
+tnep_status ensure_batch(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const int* h_offsets, int cap_R,
+                         int cap_A);
 tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const int* h_offsets, const float* d_pos,
-                        const float* d_box, const int* d_types, int types_period);
+                        const float* d_box, const int* d_types, int types_period, const ListSpec* spec = nullptr);
+tnep_status skin_lists(tnep_ctx* c, Workspace& w, Workspace& sw, cudaStream_t st, int nf, int N, const float* d_pos,
+                       const float* d_box, const int* d_types);
 tnep_status compute_moments(tnep_ctx* c, Workspace& w, cudaStream_t st, int N, bool need_v, bool need_w);
 bool any_rank(const tnep_ctx* c, int rank);
 FusedArgs fused_args(tnep_ctx* c, Workspace& w, const Model& m, int N);

@@ -400,6 +400,80 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
     if (u < a.n_types) a.seg_R[(size_t)u * a.seg_stride + i] = cnt[u];
 }
 
+// Frames of a pass in the first frame's cell order, with their boxes.
+__global__ void k_skin_gather(SkinArgs a) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)a.nf * a.N) return;
+  const int f = (int)(g / a.N), i = (int)(g % a.N);
+  const int o = a.sorted_orig[i];
+  const float* p = a.pos + ((size_t)f * a.N + o) * 3;
+  const int t = a.types[o % a.types_period];
+  a.pos4[g] = make_float4(p[0], p[1], p[2], __int_as_float(t));
+  a.sorted_struct[g] = f;
+  if (i == 0) {
+    StructBox B;
+    for (int d = 0; d < 3; ++d) {
+      const float L = a.box ? a.box[3 * f + d] : 0.0f;
+      B.L[d] = L > 0.0f ? L : 0.0f;
+      B.invL[d] = L > 0.0f ? __fdiv_rn(1.0f, L) : 0.0f;
+    }
+    a.boxes[f] = B;
+  }
+}
+
+// Each frame's exact lists from the first frame's skin lists: every skin
+// candidate is re-tested with the float32 pair rule of the header under this
+// frame's positions.  The radial list keeps the type segments; the angular
+// list is taken from the same candidates.  Flags skin_violation when an atom
+// moved more than skin / 2 from the first frame or the box changed.
+__global__ void __launch_bounds__(128) k_skin_compact(SkinArgs a) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)a.nf * a.N) return;
+  const int f = (int)(g / a.N), i = (int)(g % a.N);
+  const int base = f * a.N;
+  const float4 pi = a.pos4[g];
+  const StructBox B = a.boxes[f];
+  const StructBox R = a.ref_box[0];
+  bool bad = false;
+  for (int d = 0; d < 3; ++d) bad |= (B.L[d] != R.L[d]);
+  {
+    const float4 p0 = a.ref4[i];
+    const float dx = mi_diff(pi.x, p0.x, B.L[0], B.invL[0]);
+    const float dy = mi_diff(pi.y, p0.y, B.L[1], B.invL[1]);
+    const float dz = mi_diff(pi.z, p0.z, B.L[2], B.invL[2]);
+    bad |= (dx * dx + dy * dy + dz * dz) > a.half_skin2;
+  }
+  if (bad) atomicOr(&a.status->skin_violation, 1);
+  int cR = 0, cA = 0, start = 0;
+  for (int t = 0; t < a.n_types; ++t) {
+    const int n = a.skin_seg[(size_t)t * a.skin_seg_stride + i];
+    int kept = 0;
+    for (int e = start; e < start + n; ++e) {
+      const int j = a.skin_nbr[nbr_index(i, e, a.skin_cap)];
+      const float4 pj = a.pos4[base + j];
+      const float dx = mi_diff(pj.x, pi.x, B.L[0], B.invL[0]);
+      const float dy = mi_diff(pj.y, pi.y, B.L[1], B.invL[1]);
+      const float dz = mi_diff(pj.z, pi.z, B.L[2], B.invL[2]);
+      const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      if (r2 < a.rc2R) {
+        if (cR < a.cap_R) a.nbr_R[nbr_index((int)g, cR, a.cap_R)] = base + j;
+        ++cR;
+        ++kept;
+        if (r2 < a.rc2A) {
+          if (cA < a.cap_A) a.nbr_A[nbr_index((int)g, cA, a.cap_A)] = base + j;
+          ++cA;
+        }
+      }
+    }
+    start += n;
+    a.seg_R[(size_t)t * a.seg_stride + g] = kept;
+  }
+  a.cnt_R[g] = cR;
+  a.cnt_A[g] = cA;
+  if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
+  if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
+}
+
 __global__ void k_export(int n, const int* sorted_orig, const int* nbr_R, const int* cnt_R, int cap_R,
                          const int* nbr_A, const int* cnt_A, int cap_A, int* out_cnt_R, int* out_cnt_A,
                          int* out_R, int out_cap_R, int* out_A, int out_cap_A) {
@@ -434,6 +508,16 @@ cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st) {
     const float rc2R = a.rc_R * a.rc_R, rc2A = a.rc_A * a.rc_A;
     k_build<<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skin_compact(const SkinArgs& a, cudaStream_t st) {
+  const long long n = (long long)a.nf * a.N;
+  if (n <= 0) return cudaSuccess;
+  count_launches(2);
+  const int blocks = (int)((n + 127) / 128);
+  k_skin_gather<<<blocks, 128, 0, st>>>(a);
+  k_skin_compact<<<blocks, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ struct DevStatus {
   int bad_struct;   // structure that raised it
   int max_cnt_R;    // largest radial neighbour count seen above the cap
   int max_cnt_A;    // largest angular neighbour count seen above the cap
+  int skin_violation;  // an atom moved more than skin / 2 (or the box changed) within a pass
 };
 
 // Per-structure cell grid (orthorhombic, periodic or open per axis).
@@ -91,6 +92,24 @@ void set_last_error(const char* msg);
 // Process-wide count of kernels this library has launched.
 void count_launches(int n);
 long long launches_total();
+
+// Verlet-skin reuse within a trajectory pass (see skin_lists in engine.cu).
+struct SkinArgs {
+  int nf, N;
+  const float* pos;           // [nf][N][3] input order (device)
+  const float* box;           // [nf][3] or null
+  const int* types; int types_period;
+  int n_types;
+  const int* sorted_orig;     // first frame: sorted -> input index
+  const float4* ref4;         // first frame positions, sorted
+  const StructBox* ref_box;   // first frame box
+  const int* skin_nbr; const int* skin_seg; int skin_cap, skin_seg_stride;  // type-sorted skin lists
+  float rc2R, rc2A, half_skin2;
+  float4* pos4; int* sorted_struct; StructBox* boxes;   // batch outputs
+  int* nbr_R; int* nbr_A; int* cnt_R; int* cnt_A; int* seg_R; int seg_stride; int cap_R, cap_A;
+  DevStatus* status;
+};
+cudaError_t launch_skin_compact(const SkinArgs& a, cudaStream_t st);
 
 // Launches the cell-list + neighbour pipeline on `st`.
 cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st);

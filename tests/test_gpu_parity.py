@@ -470,3 +470,53 @@ def test_tensor_core_population_and_tail_block(tn):
             else:
                 assert err <= max(REL * np.linalg.norm(r.tensor), COND * np.abs(r.per_atom).sum())
         ctx.close()
+
+
+# ------------------------------------------------------------ Verlet skin
+def _walk(n_side, L, n_frames, sigma, seed):
+    rng = np.random.default_rng(seed)
+    base, types, box = synth.water_grid_box(n_side, L, rng)
+    frames = synth.random_walk_frames(base, box, n_frames, sigma, rng)
+    return frames, types, box.astype(np.float32)
+
+
+def test_skin_reuse_matches_per_frame_lists(tn):
+    frames, types, box = _walk(10, 31.04, 24, 0.01, 5)
+    ms, om = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_FRAMES_PER_BATCH, 8)
+    plain = tn.tnep_eval(ctx, frames, box, types)
+    assert tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_SKIN_USED) == 0
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_SKIN, 0.5)
+    skin = tn.tnep_eval(ctx, frames, box, types)
+    assert tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_SKIN_USED) == 1
+    for a, b, m in zip(plain, skin, om):
+        # same pairs, possibly another summation order
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-6 * np.abs(a).max())
+        for f in (0, 7, 23):
+            r = oracle.evaluate(m, frames[f], box, types)
+            assert np.linalg.norm(b[f] - r.tensor) <= max(REL * np.linalg.norm(r.tensor),
+                                                          COND * np.abs(r.per_atom).sum())
+    # an atom that jumps further than skin / 2 inside a pass forces fresh lists
+    jumped = frames.copy()
+    jumped[5, 17] = np.mod(jumped[5, 17] + 0.4, box)
+    skin2 = tn.tnep_eval(ctx, jumped, box, types)
+    assert tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_SKIN_USED) == 0
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_SKIN, 0.0)
+    plain2 = tn.tnep_eval(ctx, jumped, box, types)
+    for a, b in zip(plain2, skin2):
+        assert np.array_equal(a, b)
+    ctx.close()
+
+
+def test_skin_falls_back_when_box_is_short(tn):
+    frames, types, box = synth.water_small(6)  # 12.42 A < 2 (6 + 0.5) A
+    ms, _ = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    plain = tn.tnep_eval(ctx, frames, box, types)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_SKIN, 0.5)
+    skin = tn.tnep_eval(ctx, frames, box, types)
+    assert tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_SKIN_USED) == 0
+    for a, b in zip(plain, skin):
+        assert np.array_equal(a, b)
+    ctx.close()
