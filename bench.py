@@ -347,7 +347,7 @@ def main():
     ap.add_argument("--no-population", action="store_true")
     ap.add_argument("--mlp-precision", type=int, default=0)
     ap.add_argument("--precision-report", action="store_true")
-    ap.add_argument("--skin", type=float, default=0.5, help="Verlet skin of the extra skin-reuse measurement")
+    ap.add_argument("--skin", type=float, default=1.0, help="Verlet skin of the extra skin-reuse measurement")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
