@@ -38,6 +38,32 @@ PHI_R, PHI_A, PHI_ATOM = 235.0, 1380.0, 4500.0
 SMS, FP32_LANES = 152, 128
 
 
+TRAFFIC_SOURCES = ("tnep_fused.cu", "tnep_device.cuh", "tc_sm100.cuh", "tnep_internal.cuh", "radial.cu")
+
+
+def traffic_record(atoms_per_pass):
+    """DRAM bytes of the compute kernels of one pass (k_radial and both
+    k_fused launches), scaled from the ncu capture recorded under profiles/,
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    rec_path = os.path.join(ROOT, "profiles", "k_fused_traffic.txt")
+    if not os.path.exists(rec_path):
+        return None, None
+    rec = {}
+    for ln in open(rec_path):
+        if "=" in ln and not ln.startswith("#"):
+            k, v = ln.strip().split("=", 1)
+            rec[k] = v
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2312_05233_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != rec.get("sources_sha256_16"):
+        return None, None
+    per_atom = {k: float(rec[k + "_bytes_per_atom"]) for k in ("k_radial", "k_fused_rank1", "k_fused_rank2")}
+    return sum(per_atom.values()) * atoms_per_pass, per_atom
+
+
 def workload_config(n_frames):
     return {
         "workload": f"bulk water 13,824 H2O (41,472 atoms), 74.5 A periodic cube, {n_frames}-frame random walk; "
@@ -469,6 +495,9 @@ def main():
     achieved_tflops = flops_atom * atom_evals / (fused_ms * 1e-3) / 1e12 if fused_ms > 0 else None
     clocks = clk.summary()
     peak_tflops = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+    passes = fused_launches / args.steps / 2 if fused_launches else 1
+    atoms_per_pass = F * N / passes
+    traffic, traffic_per_atom = traffic_record(atoms_per_pass)
 
     units = job_units(F, N, world)
     value = units / (ms * 1e-3)
@@ -481,8 +510,11 @@ def main():
                 "d2h_bytes_per_step": int(F * 12 * 8 + 3 * 2 * (M + 1) * 8), "ms_per_step": e2e_ms},
         "gpu_launches": int(launches / args.steps),
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None, "traffic": None,
-                     "kernel": "k_fused (descriptor + network + partial force + contraction)",
+                     "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None, "traffic": traffic,
+                     "kernel": "k_radial + k_fused x2 (descriptor + network + partial force + contraction)",
+                     "traffic_scope": "DRAM bytes of k_radial and both k_fused launches of one pass "
+                                      f"({atoms_per_pass:.0f} atoms), scaled per atom from an ncu capture",
+                     "traffic_bytes_per_atom": traffic_per_atom,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
                      "flops_per_atom_eval": flops_atom, "nn_R": nn_R, "nn_A": nn_A,
                      "fused_ms_per_step": fused_ms / args.steps, "nbr_ms_per_step": nbr_ms / args.steps,
