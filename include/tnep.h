@@ -195,6 +195,64 @@ tnep_status tnep_population_eval(tnep_population* pop, const float* params, doub
 tnep_status tnep_population_info(const tnep_population* pop, double info[8]);
 void tnep_population_destroy(tnep_population* pop);
 
+/* ---- Training loop: separable natural evolution strategy (Sec. II.D) ----
+ *
+ * The paper trains the parameters z (the flat vector of tnep_model_desc.params,
+ * d = n_params entries) with SNES on the loss (Sec. II.D, dipole and
+ * polarizability losses)
+ *     L(z) = RMSE(z) + lambda1 (1/d) sum |z_i| + lambda2 sqrt((1/d) sum z_i^2),
+ * RMSE as in tnep_eval_population.  One generation, population size P:
+ *     s_k ~ N(0, I), z_k = mu + sigma * s_k;  rank by L ascending (ties: lower k
+ *     first; NaN losses rank last), rank 1 = best;
+ *     u_r = max(0, ln(P/2 + 1) - ln r) / sum_j max(0, ln(P/2 + 1) - ln j) - 1/P;
+ *     mu    += eta_mu * sigma * sum_k u_{r(k)} s_k;
+ *     sigma *= exp(eta_sigma / 2 * sum_k u_{r(k)} (s_k^2 - 1)).
+ * The normals come from Philox4x64-10 (Salmon et al. 2011): block b (entries
+ * 4b..4b+3) of individual k at generation g uses counter (b, k, g, 0) and key
+ * (seed, 0); each 64-bit output x gives u = (floor(x / 2^12) + 1/2) 2^-52, and
+ * outputs (x0, x1), (x2, x3) give sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b).
+ * mu, sigma, s and the losses are float64; each z_k is rounded to float32 for
+ * the evaluation. */
+typedef struct {
+  int n_pop;                  /* P, 2..1024 */
+  double eta_mu;              /* <= 0: 1 */
+  double eta_sigma;           /* <= 0: (3 + ln d) / (5 sqrt d) */
+  double lambda1, lambda2;    /* regularization weights, >= 0 */
+  unsigned long long seed;    /* Philox key word 0 */
+} tnep_snes_config;
+
+/* Creates a training run of model `model` of ctx on a resident structure set
+ * (arguments as tnep_population_create, host or device buffers); mu0 [d] and
+ * sigma0 [d] (host, sigma0 > 0) are the initial search distribution.  The
+ * whole generation -- sampling, evaluation of the P individuals, loss,
+ * ranking and update -- is captured once in a CUDA graph.  Errors: INVALID
+ * (bad config or buffers), OOM, CUDA, NEIGHBOR_OVERFLOW, UNSUPPORTED. */
+typedef struct tnep_snes tnep_snes;
+tnep_status tnep_snes_create(tnep_ctx* ctx, int model, const tnep_snes_config* cfg, const double* mu0,
+                             const double* sigma0, int n_structs, const int* atom_offsets, const float* pos,
+                             const float* box, const int* types, const double* target, tnep_snes** out);
+/* Runs n_gen generations on the device (one graph replay each).  history NULL
+ * or [n_gen][3] (host): loss of the best individual, its RMSE, mean loss of
+ * the population, per generation.  Synchronous. */
+tnep_status tnep_snes_run(tnep_snes* snes, int n_gen, double* history);
+/* Copies the current mu [d] and sigma [d] to host buffers (either may be
+ * NULL); *generation (may be NULL) = generations run so far. */
+tnep_status tnep_snes_state(const tnep_snes* snes, double* mu, double* sigma, long long* generation);
+/* info[4]: generations run, d, population size P, device time of the last
+ * tnep_snes_run per generation (ms). */
+tnep_status tnep_snes_info(const tnep_snes* snes, double info[4]);
+void tnep_snes_destroy(tnep_snes* snes);
+
+/* The two SNES steps alone, on device buffers, asynchronous on `stream`.
+ * tnep_snes_normals: s [n_pop][dim] float64 standard normals of `generation`.
+ * tnep_snes_update: ranks loss [n_pop] and updates mu [dim], sigma [dim] in
+ * place from s [n_pop][dim] (eta_sigma <= 0: the default for dim).
+ * n_pop in 2..1024, dim >= 1; INVALID for host pointers or bad sizes. */
+tnep_status tnep_snes_normals(unsigned long long seed, long long generation, int n_pop, int dim, double* s,
+                              void* stream);
+tnep_status tnep_snes_update(int n_pop, int dim, const double* loss, const double* s, double* mu, double* sigma,
+                             double eta_mu, double eta_sigma, void* stream);
+
 /* Spectrum kinds for tnep_spectrum. */
 enum {
   TNEP_SPECTRUM_IR = 0,          /* series [T][3] = mu(t); omega^2 * lineshape (Eq. 6) */

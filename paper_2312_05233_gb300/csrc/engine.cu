@@ -71,21 +71,30 @@ tnep_status pack_model(tnep_ctx* c, Model& m) {
 }
 
 // Flat parameters -> device layout (one individual).
-void pack_params(const Model& m, int T, const float* flat, const float* scaler, float* out) {
+// Packed word of every flat parameter (the flat order is the one documented
+// for tnep_model_desc.params); padding words and the scaler are not mapped.
+void pack_index_map(const Model& m, int T, int* dst) {
   const ModelLayout& L = m.lay;
-  std::fill(out, out + L.words, 0.f);
   size_t o = 0;
   for (int net = 0; net < m.nets; ++net) {
     for (int h = 0; h < L.H; ++h)
-      for (int d = 0; d < m.D; ++d) out[L.off_W0 + (net * L.H + h) * L.Dp + d] = flat[o++];
-    for (int h = 0; h < L.H; ++h) out[L.off_b0 + net * L.H + h] = flat[o++];
-    for (int h = 0; h < L.H; ++h) out[L.off_w1 + net * L.H + h] = flat[o++];
-    out[L.off_b1 + net] = flat[o++];
+      for (int d = 0; d < m.D; ++d) dst[o++] = L.off_W0 + (net * L.H + h) * L.Dp + d;
+    for (int h = 0; h < L.H; ++h) dst[o++] = L.off_b0 + net * L.H + h;
+    for (int h = 0; h < L.H; ++h) dst[o++] = L.off_w1 + net * L.H + h;
+    dst[o++] = L.off_b1 + net;
   }
   for (int p = 0; p < T * T; ++p)
-    for (int k = 0; k < m.nR * m.bR; ++k) out[L.off_cR + p * L.stride_cR + k] = flat[o++];
+    for (int k = 0; k < m.nR * m.bR; ++k) dst[o++] = L.off_cR + p * L.stride_cR + k;
   for (int p = 0; p < T * T; ++p)
-    for (int k = 0; k < m.nA * m.bA; ++k) out[L.off_cA + p * L.stride_cA + k] = flat[o++];
+    for (int k = 0; k < m.nA * m.bA; ++k) dst[o++] = L.off_cA + p * L.stride_cA + k;
+}
+
+void pack_params(const Model& m, int T, const float* flat, const float* scaler, float* out) {
+  const ModelLayout& L = m.lay;
+  std::fill(out, out + L.words, 0.f);
+  std::vector<int> dst(m.params.size());
+  pack_index_map(m, T, dst.data());
+  for (size_t i = 0; i < dst.size(); ++i) out[dst[i]] = flat[i];
   for (int d = 0; d < m.D; ++d) out[L.off_scaler + d] = scaler[d];
 }
 

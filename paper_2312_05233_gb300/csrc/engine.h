@@ -161,6 +161,7 @@ namespace tnep {
 
 tnep_status pack_model(tnep_ctx* c, Model& m);
 void pack_params(const Model& m, int T, const float* flat, const float* scaler, float* out);
+void pack_index_map(const Model& m, int T, int* dst);
 size_t expected_params(const tnep_model_desc& d, int T);
 tnep_status validate_model(const tnep_model_desc& d, int T);
 // Cutoffs and capacities of one list build (default: the context's).

@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -260,5 +261,217 @@ tnep_status tnep_population_info(const tnep_population* p, double info[8]) {
 }
 
 void tnep_population_destroy(tnep_population* p) { destroy_pop(p); }
+
+}  // extern "C"
+
+// ---- SNES training loop around the population evaluation (Sec. II.D) ----
+
+struct tnep_snes {
+  tnep_population* pop = nullptr;
+  int P = 0, d = 0;
+  double eta_mu = 1.0, eta_sigma = 0.0, lambda1 = 0.0, lambda2 = 0.0;
+  unsigned long long seed = 0;
+  DevBuf<double> mu, sigma, s, loss, hist;
+  DevBuf<int> dst;
+  DevBuf<long long> gen;
+  PinBuf<double> h_hist;
+  long long generation = 0;
+  double last_ms = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+tnep_status enqueue_snes(tnep_snes* sn) {
+  tnep_population* p = sn->pop;
+  const Model& m = p->ctx->models[p->model];
+  cudaStream_t st = p->stream;
+  SnesSampleArgs sa{sn->seed, sn->gen.p, sn->P, sn->d, sn->mu.p, sn->sigma.p, sn->s.p, p->d_params.p,
+                    (size_t)m.lay.words, sn->dst.p};
+  TNEP_CUDA(launch_snes_sample(sa, st));
+  TNEP_TRY(enqueue_generation(p, false));
+  SnesFitnessArgs fa{sn->P, sn->d, sn->mu.p, sn->sigma.p, sn->s.p, p->d_rmse.p, sn->lambda1, sn->lambda2,
+                     sn->loss.p};
+  TNEP_CUDA(launch_snes_fitness(fa, st));
+  SnesUpdateArgs ua{sn->P, sn->d, sn->loss.p, sn->s.p, p->d_rmse.p, sn->mu.p, sn->sigma.p, sn->eta_mu,
+                    sn->eta_sigma, sn->hist.p, sn->gen.p};
+  TNEP_CUDA(launch_snes_update(ua, st));
+  return TNEP_OK;
+}
+
+void destroy_snes(tnep_snes* sn) {
+  if (!sn) return;
+  if (sn->pop) {
+    cudaSetDevice(sn->pop->ctx->device);
+    cudaStreamSynchronize(sn->pop->stream);
+  }
+  if (sn->exec) cudaGraphExecDestroy(sn->exec);
+  if (sn->graph) cudaGraphDestroy(sn->graph);
+  sn->mu.release(); sn->sigma.release(); sn->s.release(); sn->loss.release(); sn->hist.release();
+  sn->dst.release(); sn->gen.release(); sn->h_hist.release();
+  destroy_pop(sn->pop);
+  delete sn;
+}
+
+tnep_status check_snes_sizes(int n_pop, int dim) {
+  if (n_pop < 2 || n_pop > kMaxSnesPop) return fail(TNEP_ERR_INVALID, "SNES needs 2 <= n_pop <= 1024");
+  if (dim < 1) return fail(TNEP_ERR_INVALID, "SNES needs dim >= 1");
+  return TNEP_OK;
+}
+
+double default_eta_sigma(int d) { return (3.0 + std::log((double)d)) / (5.0 * std::sqrt((double)d)); }
+
+}  // namespace
+
+extern "C" {
+
+tnep_status tnep_snes_create(tnep_ctx* ctx, int model, const tnep_snes_config* cfg, const double* mu0,
+                             const double* sigma0, int n_structs, const int* atom_offsets, const float* pos,
+                             const float* box, const int* types, const double* target, tnep_snes** out) {
+  if (!out) return fail(TNEP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !cfg || !mu0 || !sigma0) return fail(TNEP_ERR_INVALID, "NULL argument");
+  if (model < 0 || model >= (int)ctx->models.size()) return fail(TNEP_ERR_INVALID, "bad model index");
+  const int d = (int)ctx->models[model].params.size();
+  TNEP_TRY(check_snes_sizes(cfg->n_pop, d));
+  if (!(cfg->lambda1 >= 0.0) || !(cfg->lambda2 >= 0.0)) return fail(TNEP_ERR_INVALID, "lambda1, lambda2 must be >= 0");
+  if (is_device_ptr(mu0) || is_device_ptr(sigma0)) return fail(TNEP_ERR_INVALID, "mu0 and sigma0 must be host memory");
+  for (int i = 0; i < d; ++i) {
+    if (!std::isfinite(mu0[i])) return fail(TNEP_ERR_INVALID, "mu0 must be finite");
+    if (!(sigma0[i] > 0.0) || !std::isfinite(sigma0[i])) return fail(TNEP_ERR_INVALID, "sigma0 must be > 0 and finite");
+  }
+  // the population object holds the structures; its parameters start at mu0
+  std::vector<float> p0((size_t)cfg->n_pop * d);
+  for (int k = 0; k < cfg->n_pop; ++k)
+    for (int i = 0; i < d; ++i) p0[(size_t)k * d + i] = (float)mu0[i];
+  tnep_population* pop = nullptr;
+  TNEP_TRY(tnep_population_create(ctx, model, cfg->n_pop, p0.data(), n_structs, atom_offsets, pos, box, types,
+                                  target, &pop));
+  auto* sn = new (std::nothrow) tnep_snes();
+  if (!sn) {
+    destroy_pop(pop);
+    return fail(TNEP_ERR_OOM, "host allocation failed");
+  }
+  sn->pop = pop;
+  sn->P = cfg->n_pop;
+  sn->d = d;
+  sn->eta_mu = cfg->eta_mu > 0.0 ? cfg->eta_mu : 1.0;
+  sn->eta_sigma = cfg->eta_sigma > 0.0 ? cfg->eta_sigma : default_eta_sigma(d);
+  sn->lambda1 = cfg->lambda1;
+  sn->lambda2 = cfg->lambda2;
+  sn->seed = cfg->seed;
+  auto setup = [&]() -> tnep_status {
+    const Model& m = ctx->models[model];
+    cudaStream_t st = pop->stream;
+    std::vector<int> dst(d);
+    pack_index_map(m, ctx->n_types, dst.data());
+    TNEP_CUDA(sn->mu.ensure(d));
+    TNEP_CUDA(sn->sigma.ensure(d));
+    TNEP_CUDA(sn->s.ensure((size_t)sn->P * d));
+    TNEP_CUDA(sn->loss.ensure(sn->P));
+    TNEP_CUDA(sn->hist.ensure(3));
+    TNEP_CUDA(sn->dst.ensure(d));
+    TNEP_CUDA(sn->gen.ensure(1));
+    TNEP_CUDA(cudaMemcpyAsync(sn->mu.p, mu0, sizeof(double) * d, cudaMemcpyHostToDevice, st));
+    TNEP_CUDA(cudaMemcpyAsync(sn->sigma.p, sigma0, sizeof(double) * d, cudaMemcpyHostToDevice, st));
+    TNEP_CUDA(cudaMemcpyAsync(sn->dst.p, dst.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
+    TNEP_CUDA(cudaMemsetAsync(sn->gen.p, 0, sizeof(long long), st));
+    // the packed template (scaler, padding) is already on the device: the
+    // population upload of p0 wrote it for every individual
+    TNEP_CUDA(cudaMemcpyAsync(pop->d_params.p, pop->h_params.p, sizeof(float) * (size_t)sn->P * m.lay.words,
+                              cudaMemcpyHostToDevice, st));
+    TNEP_CUDA(cudaStreamSynchronize(st));
+    TNEP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const tnep_status cap = enqueue_snes(sn);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (cap != TNEP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return cap;
+    }
+    TNEP_CUDA(e);
+    sn->graph = g;
+    TNEP_CUDA(cudaGraphInstantiate(&sn->exec, g, 0));
+    return TNEP_OK;
+  };
+  const tnep_status st = setup();
+  if (st != TNEP_OK) {
+    destroy_snes(sn);
+    return st;
+  }
+  *out = sn;
+  return TNEP_OK;
+}
+
+tnep_status tnep_snes_run(tnep_snes* sn, int n_gen, double* history) {
+  if (!sn || n_gen < 0) return fail(TNEP_ERR_INVALID, "bad SNES handle or n_gen");
+  if (n_gen == 0) return TNEP_OK;
+  tnep_population* p = sn->pop;
+  TNEP_CUDA(cudaSetDevice(p->ctx->device));
+  cudaStream_t st = p->stream;
+  if (history) TNEP_CUDA(sn->h_hist.ensure((size_t)3 * n_gen));
+  TNEP_CUDA(cudaEventRecord(p->ev0, st));
+  for (int g = 0; g < n_gen; ++g) {
+    TNEP_CUDA(cudaGraphLaunch(sn->exec, st));
+    if (history)
+      TNEP_CUDA(cudaMemcpyAsync(sn->h_hist.p + 3 * (size_t)g, sn->hist.p, 3 * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+  }
+  TNEP_CUDA(cudaEventRecord(p->ev1, st));
+  TNEP_CUDA(cudaStreamSynchronize(st));
+  count_launches(7 * n_gen);  // sample, fused, two reduction stages, RMSE, fitness, update
+  float ms = 0.f;
+  TNEP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+  sn->last_ms = ms / n_gen;
+  sn->generation += n_gen;
+  if (history) std::memcpy(history, sn->h_hist.p, sizeof(double) * 3 * (size_t)n_gen);
+  return TNEP_OK;
+}
+
+tnep_status tnep_snes_state(const tnep_snes* sn, double* mu, double* sigma, long long* generation) {
+  if (!sn) return fail(TNEP_ERR_INVALID, "NULL SNES handle");
+  if ((mu && is_device_ptr(mu)) || (sigma && is_device_ptr(sigma)))
+    return fail(TNEP_ERR_INVALID, "mu and sigma must be host memory");
+  TNEP_CUDA(cudaSetDevice(sn->pop->ctx->device));
+  TNEP_CUDA(cudaStreamSynchronize(sn->pop->stream));
+  if (mu) TNEP_CUDA(cudaMemcpy(mu, sn->mu.p, sizeof(double) * sn->d, cudaMemcpyDeviceToHost));
+  if (sigma) TNEP_CUDA(cudaMemcpy(sigma, sn->sigma.p, sizeof(double) * sn->d, cudaMemcpyDeviceToHost));
+  if (generation) *generation = sn->generation;
+  return TNEP_OK;
+}
+
+tnep_status tnep_snes_info(const tnep_snes* sn, double info[4]) {
+  if (!sn || !info) return fail(TNEP_ERR_INVALID, "NULL argument");
+  info[0] = (double)sn->generation;
+  info[1] = sn->d;
+  info[2] = sn->P;
+  info[3] = sn->last_ms;
+  return TNEP_OK;
+}
+
+void tnep_snes_destroy(tnep_snes* sn) { destroy_snes(sn); }
+
+tnep_status tnep_snes_normals(unsigned long long seed, long long generation, int n_pop, int dim, double* s,
+                              void* stream) {
+  TNEP_TRY(check_snes_sizes(n_pop, dim));
+  if (generation < 0) return fail(TNEP_ERR_INVALID, "generation must be >= 0");
+  if (!s || !is_device_ptr(s)) return fail(TNEP_ERR_INVALID, "s must be device memory");
+  TNEP_CUDA(launch_snes_normals(seed, generation, n_pop, dim, s, (cudaStream_t)stream));
+  return TNEP_OK;
+}
+
+tnep_status tnep_snes_update(int n_pop, int dim, const double* loss, const double* s, double* mu, double* sigma,
+                             double eta_mu, double eta_sigma, void* stream) {
+  TNEP_TRY(check_snes_sizes(n_pop, dim));
+  for (const void* q : {(const void*)loss, (const void*)s, (const void*)mu, (const void*)sigma})
+    if (!q || !is_device_ptr(q)) return fail(TNEP_ERR_INVALID, "loss, s, mu and sigma must be device memory");
+  if (!(eta_mu > 0.0)) return fail(TNEP_ERR_INVALID, "eta_mu must be > 0");
+  SnesUpdateArgs ua{n_pop, dim, loss, s, nullptr, mu, sigma, eta_mu,
+                    eta_sigma > 0.0 ? eta_sigma : default_eta_sigma(dim), nullptr, nullptr};
+  TNEP_CUDA(launch_snes_update(ua, (cudaStream_t)stream));
+  count_launches(1);
+  return TNEP_OK;
+}
 
 }  // extern "C"

@@ -198,4 +198,42 @@ cudaError_t launch_spectrum(const double* series, int T, int C, double dt_fs, in
                             int subtract_mean, double* work /* >= T*9 + 2*(M+1) + 2*M doubles */,
                             double* freq, double* spec, double* acf_out, cudaStream_t st);
 
+// SNES training loop (snes.cu).
+constexpr int kMaxSnesPop = 1024;
+struct SnesSampleArgs {
+  uint64_t seed;
+  const long long* generation;  // device counter
+  int P, d;
+  const double* mu;
+  const double* sigma;
+  double* s;          // [P][d]
+  float* packed;      // [P][words] packed parameters of the fused kernel
+  size_t words;
+  const int* dst;     // packed word of flat parameter i
+};
+struct SnesFitnessArgs {
+  int P, d;
+  const double* mu;
+  const double* sigma;
+  const double* s;
+  const double* rmse;
+  double lambda1, lambda2;
+  double* loss;
+};
+struct SnesUpdateArgs {
+  int P, d;
+  const double* loss;
+  const double* s;
+  const double* rmse;   // may be null
+  double* mu;
+  double* sigma;
+  double eta_mu, eta_sigma;
+  double* history;      // [3] or null
+  long long* generation;  // advanced by one, or null
+};
+cudaError_t launch_snes_normals(uint64_t seed, long long generation, int P, int d, double* s, cudaStream_t st);
+cudaError_t launch_snes_sample(const SnesSampleArgs& a, cudaStream_t st);
+cudaError_t launch_snes_fitness(const SnesFitnessArgs& a, cudaStream_t st);
+cudaError_t launch_snes_update(const SnesUpdateArgs& a, cudaStream_t st);
+
 }  // namespace tnep

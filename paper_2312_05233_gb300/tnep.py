@@ -37,6 +37,8 @@ EXPORTED = [
     "tnep_set_option", "tnep_get_option", "tnep_spectrum_noalloc",
     "tnep_server_start", "tnep_submit", "tnep_poll", "tnep_wait", "tnep_server_stats", "tnep_server_stop",
     "tnep_population_create", "tnep_population_eval", "tnep_population_info", "tnep_population_destroy",
+    "tnep_snes_create", "tnep_snes_run", "tnep_snes_state", "tnep_snes_info", "tnep_snes_destroy",
+    "tnep_snes_normals", "tnep_snes_update",
 ]
 TNEP_NOALLOC_MAX_T = 32768
 
@@ -58,6 +60,11 @@ class ModelDesc(C.Structure):
         ("per_type_nn", C.c_int), ("params", C.POINTER(C.c_float)), ("n_params", C.c_size_t),
         ("q_scaler", C.POINTER(C.c_float)), ("mlp_precision", C.c_int),
     ]
+
+
+class SnesConfig(C.Structure):
+    _fields_ = [("n_pop", C.c_int), ("eta_mu", C.c_double), ("eta_sigma", C.c_double),
+                ("lambda1", C.c_double), ("lambda2", C.c_double), ("seed", C.c_ulonglong)]
 
 
 def _load():
@@ -88,6 +95,14 @@ def _load():
         "tnep_population_eval": (C.c_int, [vp, fp, dp, dp]),
         "tnep_population_info": (C.c_int, [vp, dp]),
         "tnep_population_destroy": (None, [vp]),
+        "tnep_snes_create": (C.c_int, [vp, C.c_int, C.POINTER(SnesConfig), dp, dp, C.c_int, ip, fp, fp, vp, dp,
+                                       C.POINTER(vp)]),
+        "tnep_snes_run": (C.c_int, [vp, C.c_int, dp]),
+        "tnep_snes_state": (C.c_int, [vp, dp, dp, C.POINTER(C.c_longlong)]),
+        "tnep_snes_info": (C.c_int, [vp, dp]),
+        "tnep_snes_destroy": (None, [vp]),
+        "tnep_snes_normals": (C.c_int, [C.c_ulonglong, C.c_longlong, C.c_int, C.c_int, dp, vp]),
+        "tnep_snes_update": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -487,3 +502,81 @@ def tnep_population_create(ctx: Context, model: int, params, offsets, pos, box, 
                                        offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr, T.ptr, TG.ptr,
                                        C.byref(h)))
     return Population(h, prm.shape[0], S, ctx.dims[model])
+
+
+class Snes:
+    """Owns a tnep_snes handle: the SNES training loop on resident structures."""
+
+    def __init__(self, handle, n_pop, dim):
+        self.handle = handle
+        self.n_pop, self.dim = n_pop, dim
+
+    def run(self, n_gen):
+        """Runs n_gen generations; returns history [n_gen][3] (best loss, its RMSE, mean loss)."""
+        hist = np.zeros((max(int(n_gen), 0), 3))
+        _check(_lib.tnep_snes_run(self.handle, int(n_gen), hist.ctypes.data if n_gen > 0 else None))
+        return hist
+
+    def state(self):
+        mu = np.zeros(self.dim)
+        sigma = np.zeros(self.dim)
+        g = C.c_longlong()
+        _check(_lib.tnep_snes_state(self.handle, mu.ctypes.data, sigma.ctypes.data, C.byref(g)))
+        return mu, sigma, g.value
+
+    def info(self):
+        v = np.zeros(4)
+        _check(_lib.tnep_snes_info(self.handle, v.ctypes.data))
+        return dict(generation=int(v[0]), dim=int(v[1]), n_pop=int(v[2]), ms_per_generation=v[3])
+
+    def close(self):
+        if self.handle:
+            _lib.tnep_snes_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tnep_snes_create(ctx: Context, model: int, n_pop, mu0, sigma0, offsets, pos, box, types, target,
+                     seed=0, eta_mu=0.0, eta_sigma=0.0, lambda1=0.0, lambda2=0.0) -> Snes:
+    mu = np.ascontiguousarray(mu0, dtype=np.float64)
+    sg = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma0, dtype=np.float64), mu.shape))
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    T = _Buf(types, np.int32, "types")
+    TG = _Buf(target, np.float64, "target")
+    cfg = SnesConfig(int(n_pop), float(eta_mu), float(eta_sigma), float(lambda1), float(lambda2), int(seed))
+    h = C.c_void_p()
+    _check(_lib.tnep_snes_create(ctx.handle, int(model), C.byref(cfg), mu.ctypes.data, sg.ctypes.data, S,
+                                 offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr, T.ptr, TG.ptr,
+                                 C.byref(h)))
+    return Snes(h, int(n_pop), mu.size)
+
+
+def tnep_snes_normals(seed, generation, n_pop, dim, s, stream=None):
+    """Fills the device tensor s [n_pop][dim] (float64) with the generation's normals."""
+    S = _Buf(s, np.float64, "s", writable=True)
+    _check(_lib.tnep_snes_normals(int(seed), int(generation), int(n_pop), int(dim), S.ptr, _stream_ptr(stream)))
+
+
+def tnep_snes_update(loss, s, mu, sigma, eta_mu=1.0, eta_sigma=0.0, stream=None):
+    """In-place SNES update of the device tensors mu, sigma [dim] from s [P][dim] and loss [P]."""
+    L = _Buf(loss, np.float64, "loss")
+    S = _Buf(s, np.float64, "s")
+    M = _Buf(mu, np.float64, "mu", writable=True)
+    G = _Buf(sigma, np.float64, "sigma", writable=True)
+    n_pop, dim = int(np.shape(s)[0]) if s is not None else 0, int(np.shape(s)[1]) if s is not None else 0
+    _check(_lib.tnep_snes_update(n_pop, dim, L.ptr, S.ptr, M.ptr, G.ptr, float(eta_mu), float(eta_sigma),
+                                 _stream_ptr(stream)))

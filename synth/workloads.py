@@ -37,7 +37,7 @@ __all__ = [
     "bzo_supercell", "thermal_frames", "water_cluster", "anion",
     "poisson_arrivals", "Structure", "StructureBatch", "concat_structures",
     "water_small", "water_bulk", "bzo_perovskite", "population_structures",
-    "serving_requests",
+    "serving_requests", "snes_update_inputs", "tensor_targets",
 ]
 
 
@@ -330,3 +330,23 @@ def serving_requests(n: int, rng: np.random.Generator, max_mol: int = 8000):
             t = np.where(t == 0, 3, 0).astype(np.int32)
         out.append(Structure(p.astype(np.float32), t.astype(np.int32), b.astype(np.float32)))
     return out
+
+
+def tensor_targets(n_structs: int, width: int, rng: np.random.Generator) -> np.ndarray:
+    """Reference tensors for training-style runs: N(0, 1) per component."""
+    return rng.standard_normal((n_structs, width))
+
+
+def snes_update_inputs(n_pop: int, dim: int, rng: np.random.Generator, ties: bool = True, nan: bool = False):
+    """Inputs of one SNES update: mean, step sizes, samples and losses.  With
+    `ties`, some losses repeat exactly; with `nan`, one loss is NaN."""
+    mu = rng.standard_normal(dim)
+    sigma = rng.uniform(0.05, 0.5, dim)
+    s = rng.standard_normal((n_pop, dim))
+    loss = rng.uniform(0.5, 2.0, n_pop)
+    if ties and n_pop >= 4:
+        loss[1] = loss[0]
+        loss[n_pop - 1] = loss[2]
+    if nan and n_pop >= 3:
+        loss[n_pop // 2] = np.nan
+    return mu, sigma, s, loss

@@ -93,3 +93,23 @@ def test_null_context_and_spectrum_validation(tn):
     assert lib.tnep_spectrum(s.ctypes.data, 10, 3, 1.0, 0, 10, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
     assert lib.tnep_spectrum(s.ctypes.data, 10, 3, 1.0, 7, 5, 1, f.ctypes.data, sp.ctypes.data, None, None) == 1
     assert "kind" in lib.tnep_last_error().decode()
+
+
+def test_snes_validation(tn):
+    lib = tn.lib()
+    buf = np.zeros(64)
+    # population size 2..1024, dim >= 1, device buffers only
+    assert lib.tnep_snes_normals(1, 0, 1, 8, buf.ctypes.data, None) == 1
+    assert lib.tnep_snes_normals(1, 0, 1025, 8, buf.ctypes.data, None) == 1
+    assert lib.tnep_snes_normals(1, 0, 4, 0, buf.ctypes.data, None) == 1
+    assert lib.tnep_snes_normals(1, -1, 4, 8, buf.ctypes.data, None) == 1
+    assert lib.tnep_snes_normals(1, 0, 4, 8, buf.ctypes.data, None) == 1  # host pointer
+    assert "device" in lib.tnep_last_error().decode()
+    assert lib.tnep_snes_update(4, 8, buf.ctypes.data, buf.ctypes.data, buf.ctypes.data, buf.ctypes.data,
+                                1.0, 0.0, None) == 1
+    cfg = tn.SnesConfig(8, 0.0, 0.0, 0.0, 0.0, 1)
+    h = C.c_void_p()
+    assert lib.tnep_snes_create(None, 0, C.byref(cfg), buf.ctypes.data, buf.ctypes.data, 1, None, None, None,
+                                None, None, C.byref(h)) == 1
+    assert lib.tnep_snes_run(None, 1, None) == 1
+    assert lib.tnep_snes_info(None, buf.ctypes.data) == 1
