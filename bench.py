@@ -263,6 +263,36 @@ def population_bench(tn, synth, device, n_pop=50, gens=5):
             "candidates_ms": info["tune_ms"], "rmse_first": float(rmse[0])}
 
 
+def snes_bench(tn, synth, device, n_pop=50, gens=100):
+    """The SNES training loop on the population workload: 50 individuals x
+    600 structures per generation, dipole loss against seeded random targets
+    with L1 / L2 terms (lambda 2e-3 each); every generation (sampling,
+    evaluation, loss, ranking, update) is one CUDA graph replay."""
+    rng = np.random.default_rng(synth.seed_for(4, 10))
+    structs = synth.population_structures()
+    bt = synth.concat_structures(structs)
+    hp = synth.HyperParams(n_types=2, rank=1)
+    sc = synth.default_q_scaler(hp)
+    target = synth.tensor_targets(bt.n_structs, 3, rng)
+    mu0 = synth.model_params(hp, rng).astype(np.float64)
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, mu0.astype(np.float32), sc)], 2, RC, device=device)
+    sn = tn.tnep_snes_create(ctx, 0, n_pop, mu0, 0.1, bt.offsets, bt.pos, bt.box, bt.types, target, seed=11,
+                             lambda1=2e-3, lambda2=2e-3)
+    sn.run(3)
+    t0 = time.perf_counter()
+    hist = sn.run(gens)
+    wall = (time.perf_counter() - t0) / gens
+    info = sn.info()
+    sn.close()
+    ctx.close()
+    atoms = len(bt.types)
+    return {"workload": f"SNES, {n_pop} individuals x {bt.n_structs} structures ({atoms} atoms), rank 1, "
+                        f"d = {info['dim']}, {gens} generations",
+            "generation_ms": wall * 1e3, "generation_device_ms": info["ms_per_generation"],
+            "generations_per_s": 1.0 / wall, "atom_evals_per_s": n_pop * atoms / wall,
+            "best_loss_first": float(hist[0, 0]), "best_loss_last": float(hist[-1, 0])}
+
+
 def precision_report(tn, synth, device, n_frames=500, oracle_frames=1):
     """BaZrO3 12x12x12 (8,640 atoms), 500 frames, rank-2 susceptibility:
     the network on the CUDA cores in FP32 (mode 0), on the tensor cores in
@@ -526,6 +556,8 @@ def main():
         line["precision"] = precision_report(tn, synth, local)
     if rank == 0 and not args.no_population:
         line["population"] = population_bench(tn, synth, local)
+    if rank == 0 and not args.no_population:
+        line["snes"] = snes_bench(tn, synth, local)
     if rank == 0 and not args.no_serve:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["served"] = serving_bench(tn, synth, local, rates, args.serve_requests)
