@@ -5,3 +5,4 @@ and reference legs; never by the product package.
 """
 from .tnep_oracle import *  # noqa: F401,F403
 from .snes_oracle import *  # noqa: F401,F403
+from .raman_oracle import *  # noqa: F401,F403

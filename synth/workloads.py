@@ -37,7 +37,7 @@ __all__ = [
     "bzo_supercell", "thermal_frames", "water_cluster", "anion",
     "poisson_arrivals", "Structure", "StructureBatch", "concat_structures",
     "water_small", "water_bulk", "bzo_perovskite", "population_structures",
-    "serving_requests", "snes_update_inputs", "tensor_targets",
+    "serving_requests", "snes_update_inputs", "tensor_targets", "tensor_series",
 ]
 
 
@@ -350,3 +350,28 @@ def snes_update_inputs(n_pop: int, dim: int, rng: np.random.Generator, ties: boo
     if nan and n_pop >= 3:
         loss[n_pop // 2] = np.nan
     return mu, sigma, s, loss
+
+
+def tensor_series(n_steps: int, rng: np.random.Generator, n_modes: int = 4, dt_fs: float = 5.0,
+                  symmetric: bool = True) -> np.ndarray:
+    """A synthetic polarizability / susceptibility trajectory [T][9]: a
+    constant tensor plus damped, randomly re-excited oscillators (AR(2)
+    processes at 100-900 cm^-1) with random tensor amplitudes, plus white
+    noise; symmetric tensors unless asked otherwise."""
+    c_cm_fs = 2.99792458e-5
+    base = rng.standard_normal((3, 3))
+    out = np.zeros((n_steps, 3, 3)) + base
+    for _ in range(n_modes):
+        w = 2 * np.pi * rng.uniform(100, 900) * c_cm_fs * dt_fs  # rad per step
+        r = np.exp(-rng.uniform(0.002, 0.02))
+        a1, a2 = 2 * r * np.cos(w), -r * r
+        drive = rng.standard_normal(n_steps)
+        x = np.zeros(n_steps)
+        for t in range(2, n_steps):
+            x[t] = a1 * x[t - 1] + a2 * x[t - 2] + drive[t]
+        amp = rng.standard_normal((3, 3))
+        out += x[:, None, None] * amp * 0.05
+    out += 0.01 * rng.standard_normal(out.shape)
+    if symmetric:
+        out = 0.5 * (out + out.transpose(0, 2, 1))
+    return out.reshape(n_steps, 9)
