@@ -293,6 +293,26 @@ def snes_bench(tn, synth, device, n_pop=50, gens=100):
             "best_loss_first": float(hist[0, 0]), "best_loss_last": float(hist[-1, 0])}
 
 
+def raman_bench(tn, synth, T=100_000, M=2000, n_theta=181):
+    """Polarized Raman tail at the BaZrO3 production length: a synthetic
+    susceptibility trajectory of 100,000 samples (500 ps at 5 fs), lineshape
+    tensor up to 10 ps lag, then the Z(XX)Z-bar / Z(XY)Z-bar orientation map
+    for 181 crystal angles about z.  Wall time of the synchronous calls,
+    host series in, host spectra out."""
+    a = synth.tensor_series(T, np.random.default_rng(synth.seed_for(7, 5)))
+    tn.tnep_raman_tensor(a[:4000], 5.0, 100)  # warm-up
+    t0 = time.perf_counter()
+    _, L = tn.tnep_raman_tensor(a, 5.0, M)
+    t1 = time.perf_counter()
+    th = np.linspace(0.0, np.pi, n_theta)
+    tn.tnep_raman_porto_map(L, th, 2)
+    t2 = time.perf_counter()
+    fma = 81.0 * T * (M + 1) - 81.0 * M * (M + 1) / 2
+    return {"workload": f"susceptibility series T = {T} (500 ps at 5 fs), M = {M} lags, {n_theta} angles",
+            "tensor_ms": (t1 - t0) * 1e3, "porto_map_ms": (t2 - t1) * 1e3,
+            "fp64_gflops": 2 * fma / (t1 - t0) / 1e9}
+
+
 def precision_report(tn, synth, device, n_frames=500, oracle_frames=1):
     """BaZrO3 12x12x12 (8,640 atoms), 500 frames, rank-2 susceptibility:
     the network on the CUDA cores in FP32 (mode 0), on the tensor cores in
@@ -558,6 +578,8 @@ def main():
         line["population"] = population_bench(tn, synth, local)
     if rank == 0 and not args.no_population:
         line["snes"] = snes_bench(tn, synth, local)
+    if rank == 0 and not args.no_population:
+        line["raman"] = raman_bench(tn, synth)
     if rank == 0 and not args.no_serve:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["served"] = serving_bench(tn, synth, local, rates, args.serve_requests)

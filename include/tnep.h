@@ -307,6 +307,39 @@ tnep_status tnep_server_stats(tnep_server* server, double stats[6]);
 /* Finishes admitted requests (bounded by their device work), then frees the server. */
 void tnep_server_stop(tnep_server* server);
 
+/* Polarized Raman (Sec. II.G).  The Stokes cross-section for observed
+ * polarization n and incoming polarization eps is
+ *     sum_{gamma delta mu nu} n_gamma eps_delta n_mu eps_nu L_{gamma delta mu nu}(omega)   (Eq. 7)
+ * with L the Fourier transform of <alpha_{gamma delta}(0) alpha_{mu nu}(t)> (Eq. 8).
+ * tnep_raman_tensor computes, for p = (gamma, delta), q = (mu, nu) (row-major
+ * index 3 gamma + delta) and tau = 0..M,
+ *     C_pq(tau) = 1/(T - tau) sum_{t=0}^{T-1-tau} a_p(t) a_q(t + tau)
+ * (each component's mean removed first when subtract_mean != 0) and keeps the
+ * part every polarization contraction sees, S_pq = (C_pq + C_qp) / 2, with the
+ * cosine transform of tnep_spectrum:
+ *     L_pq(nu_k) = dt [S_pq(0) + 2 sum_{tau=1}^{M} S_pq(tau) cos(pi k tau / M)],
+ * nu_k = k / (2 M dt), M = max_lag (<= 0: T/2), 0 < M < T.
+ *   series   [T][9] float64 alpha(t) or chi(t), row-major 3x3 (host or device)
+ *   freq_cm1 [M+1], L [M+1][9][9] (host or device).  Synchronous.
+ * Cost: 81 T (M+1) float64 multiply-adds (direct time-origin sums). */
+tnep_status tnep_raman_tensor(const double* series, int T, double dt_fs, int max_lag, int subtract_mean,
+                              double* freq_cm1, double* L, void* stream);
+/* Eq. 7 for n_orient pairs of polarization vectors: n, eps [n_orient][3]
+ * (any length; the contraction is quadratic in each), L [max_lag+1][9][9]
+ * from tnep_raman_tensor, spec [n_orient][max_lag+1].  Host or device
+ * buffers.  Synchronous. */
+tnep_status tnep_raman_polarized(const double* L, int max_lag, int n_orient, const double* n, const double* eps,
+                                 double* spec, void* stream);
+/* Orientation map in Porto notation (Sec. IV, BaZrO3): for a crystal turned
+ * by theta (radians) about crystal axis `axis` (0, 1, 2 = x, y, z; the laser
+ * direction), with X, Y the next two axes in cyclic order, the incoming
+ * polarization is R^T X = cos(theta) X - sin(theta) Y and the observed one is
+ * R^T X for Z(XX)Z-bar (spec_parallel) or R^T Y = sin(theta) X + cos(theta) Y
+ * for Z(XY)Z-bar (spec_crossed); both [n_theta][max_lag+1].  Host or device
+ * buffers.  Synchronous. */
+tnep_status tnep_raman_porto_map(const double* L, int max_lag, int n_theta, const double* theta, int axis,
+                                 double* spec_parallel, double* spec_crossed, void* stream);
+
 /* Longest series tnep_spectrum_noalloc accepts (its scratch is sized for it). */
 #define TNEP_NOALLOC_MAX_T 32768
 

@@ -39,6 +39,7 @@ EXPORTED = [
     "tnep_population_create", "tnep_population_eval", "tnep_population_info", "tnep_population_destroy",
     "tnep_snes_create", "tnep_snes_run", "tnep_snes_state", "tnep_snes_info", "tnep_snes_destroy",
     "tnep_snes_normals", "tnep_snes_update",
+    "tnep_raman_tensor", "tnep_raman_polarized", "tnep_raman_porto_map",
 ]
 TNEP_NOALLOC_MAX_T = 32768
 
@@ -103,6 +104,9 @@ def _load():
         "tnep_snes_destroy": (None, [vp]),
         "tnep_snes_normals": (C.c_int, [C.c_ulonglong, C.c_longlong, C.c_int, C.c_int, dp, vp]),
         "tnep_snes_update": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, vp]),
+        "tnep_raman_tensor": (C.c_int, [dp, C.c_int, C.c_double, C.c_int, C.c_int, dp, dp, vp]),
+        "tnep_raman_polarized": (C.c_int, [dp, C.c_int, C.c_int, dp, dp, dp, vp]),
+        "tnep_raman_porto_map": (C.c_int, [dp, C.c_int, C.c_int, dp, C.c_int, dp, dp, vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -580,3 +584,42 @@ def tnep_snes_update(loss, s, mu, sigma, eta_mu=1.0, eta_sigma=0.0, stream=None)
     n_pop, dim = int(np.shape(s)[0]) if s is not None else 0, int(np.shape(s)[1]) if s is not None else 0
     _check(_lib.tnep_snes_update(n_pop, dim, L.ptr, S.ptr, M.ptr, G.ptr, float(eta_mu), float(eta_sigma),
                                  _stream_ptr(stream)))
+
+
+def tnep_raman_tensor(series, dt_fs, max_lag=0, subtract_mean=True, stream=None):
+    """Returns (freq_cm1 [M+1], L [M+1][9][9]) as numpy arrays."""
+    S = _Buf(series, np.float64, "series")
+    T = int(np.shape(series)[0])
+    M = int(max_lag) if max_lag and max_lag > 0 else T // 2
+    freq = np.zeros(M + 1)
+    L = np.zeros((M + 1, 9, 9))
+    _check(_lib.tnep_raman_tensor(S.ptr, T, float(dt_fs), M, int(bool(subtract_mean)), freq.ctypes.data,
+                                  L.ctypes.data, _stream_ptr(stream)))
+    return freq, L
+
+
+def tnep_raman_polarized(L, n, eps, stream=None):
+    """spec [n_orient][M+1] for the rows of n and eps."""
+    Lb = _Buf(L, np.float64, "L")
+    nb = _Buf(np.atleast_2d(np.asarray(n, dtype=np.float64)), np.float64, "n")
+    eb = _Buf(np.atleast_2d(np.asarray(eps, dtype=np.float64)), np.float64, "eps")
+    M = int(np.shape(L)[0]) - 1
+    O = nb.obj.shape[0]
+    if eb.obj.shape[0] != O:
+        raise ValueError("n and eps need the same number of rows")
+    out = np.zeros((O, M + 1))
+    _check(_lib.tnep_raman_polarized(Lb.ptr, M, O, nb.ptr, eb.ptr, out.ctypes.data, _stream_ptr(stream)))
+    return out
+
+
+def tnep_raman_porto_map(L, thetas, axis=2, stream=None):
+    """(parallel, crossed) spectra [n_theta][M+1] for crystal rotations theta (rad) about `axis`."""
+    Lb = _Buf(L, np.float64, "L")
+    th = _Buf(np.atleast_1d(np.asarray(thetas, dtype=np.float64)), np.float64, "thetas")
+    M = int(np.shape(L)[0]) - 1
+    O = th.obj.shape[0]
+    par = np.zeros((O, M + 1))
+    crs = np.zeros((O, M + 1))
+    _check(_lib.tnep_raman_porto_map(Lb.ptr, M, O, th.ptr, int(axis), par.ctypes.data, crs.ctypes.data,
+                                     _stream_ptr(stream)))
+    return par, crs

@@ -113,3 +113,19 @@ def test_snes_validation(tn):
                                 None, None, C.byref(h)) == 1
     assert lib.tnep_snes_run(None, 1, None) == 1
     assert lib.tnep_snes_info(None, buf.ctypes.data) == 1
+
+
+def test_raman_validation(tn):
+    lib = tn.lib()
+    s = np.zeros((10, 9))
+    f = np.zeros(6)
+    L = np.zeros((6, 81))
+    assert lib.tnep_raman_tensor(s.ctypes.data, 1, 1.0, 0, 1, f.ctypes.data, L.ctypes.data, None) == 1
+    assert lib.tnep_raman_tensor(s.ctypes.data, 10, 0.0, 5, 1, f.ctypes.data, L.ctypes.data, None) == 1
+    assert lib.tnep_raman_tensor(s.ctypes.data, 10, 1.0, 10, 1, f.ctypes.data, L.ctypes.data, None) == 1
+    assert lib.tnep_raman_tensor(None, 10, 1.0, 5, 1, f.ctypes.data, L.ctypes.data, None) == 1
+    v = np.zeros(3)
+    assert lib.tnep_raman_polarized(L.ctypes.data, 5, 0, v.ctypes.data, v.ctypes.data, f.ctypes.data, None) == 1
+    assert lib.tnep_raman_porto_map(L.ctypes.data, 5, 1, v.ctypes.data, 3, f.ctypes.data, f.ctypes.data,
+                                    None) == 1
+    assert "axis" in lib.tnep_last_error().decode()
