@@ -73,7 +73,7 @@ WAVENUMBER_PER_INV_FS = 1.0 / 2.99792458e-5  # 1 fs^-1 in cm^-1
 __all__ = [
     "OracleModel", "pairs_fp64", "neighbours_fp32", "wigner3j",
     "sph_harm_complex", "evaluate", "evaluate_frames", "site_energies_from_pairs",
-    "acf", "spectrum", "KIND_IR", "KIND_RAMAN_ISO", "KIND_RAMAN_ANISO",
+    "acf", "spectrum", "KIND_IR", "KIND_RAMAN_ISO", "KIND_RAMAN_ANISO", "com_dipole",
 ]
 
 KIND_IR, KIND_RAMAN_ISO, KIND_RAMAN_ANISO = 0, 1, 2
@@ -457,6 +457,18 @@ def evaluate_frames(m: OracleModel, frames, box, types, mode="factorized"):
         b = box if box is None or np.ndim(box) == 1 else box[f]
         out.append(evaluate(m, frames[f], b, types, mode=mode).tensor)
     return np.asarray(out)
+
+
+# --------------------------------------------------------------------------
+# charged molecules (Sec. III.A)
+# --------------------------------------------------------------------------
+def com_dipole(pos, types, masses, charge):
+    """Q r_COM, the term that turns the relative dipole mu_r of a molecule
+    with net charge Q (in e) into its dipole about the origin,
+    mu = mu_r + Q r_COM, r_COM = sum_i m_i r_i / sum_i m_i (Sec. III.A)."""
+    r = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    m = np.asarray(masses, dtype=np.float64)[np.asarray(types)]
+    return float(charge) * (m[:, None] * r).sum(0) / m.sum()
 
 
 # --------------------------------------------------------------------------

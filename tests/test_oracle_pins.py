@@ -348,3 +348,21 @@ def test_raman_iso_aniso_split():
     Bc = B - B.mean(0)
     ref = np.einsum("tab,tba->", Bc[:-2], Bc[2:]) / (T - 2)
     assert oracle.acf(B.reshape(T, 9), 20, oracle.KIND_RAMAN_ANISO)[2] == pytest.approx(ref, rel=1e-12)
+
+
+def test_com_dipole_closed_forms():
+    rng = np.random.default_rng(12)
+    pos = rng.normal(size=(7, 3))
+    types = np.array([0, 1, 1, 2, 0, 1, 2])
+    masses = np.array([15.999, 1.008, 12.011])
+    q = -1.0
+    base = oracle.com_dipole(pos, types, masses, q)
+    d = np.array([0.3, -1.2, 2.5])
+    # translating the molecule by d moves the origin-referenced dipole by Q d
+    np.testing.assert_allclose(oracle.com_dipole(pos + d, types, masses, q) - base, q * d, atol=1e-12)
+    # neutral: no correction; one atom: Q r; equal masses: Q times the centroid
+    assert np.all(oracle.com_dipole(pos, types, masses, 0.0) == 0.0)
+    np.testing.assert_allclose(oracle.com_dipole(pos[:1], types[:1], masses, 2.0), 2.0 * pos[0])
+    np.testing.assert_allclose(oracle.com_dipole(pos, np.zeros(7, int), masses, 1.0), pos.mean(0), atol=1e-14)
+    # only mass ratios matter
+    np.testing.assert_allclose(oracle.com_dipole(pos, types, 3.7 * masses, q), base, atol=1e-13)
