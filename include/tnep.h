@@ -253,6 +253,24 @@ tnep_status tnep_snes_normals(unsigned long long seed, long long generation, int
 tnep_status tnep_snes_update(int n_pop, int dim, const double* loss, const double* s, double* mu, double* sigma,
                              double eta_mu, double eta_sigma, void* stream);
 
+/* Charged molecules (Sec. III.A): the dipole of a molecule with net charge Q
+ * depends on the reference point, so dipole models are trained on the dipole
+ * relative to the centre of mass, mu_r; the dipole about the origin is
+ *     mu = mu_r + Q r_COM,   r_COM = sum_i m_i r_i / sum_i m_i.
+ * tnep_set_masses stores one mass per type (any unit; only ratios matter).
+ * tnep_add_com_dipole adds Q_s r_COM,s to mu[s * mu_stride + 0..2] in place for
+ * each structure s of a batch (layout of tnep_eval_batch: pass
+ * out + column offset of the rank-1 model and mu_stride = total width).
+ *   charge [n_structs] float64 in e (0 = neutral, left unchanged); a charged
+ *   structure must be open (box row 0 0 0, checked for host buffers).
+ *   atom_offsets host; pos, box (may be NULL = all open), types, charge, mu
+ *   host or device.  Sums in float64, fixed order.  Synchronous.
+ * Errors: INVALID (no masses set, bad sizes, charged periodic structure). */
+tnep_status tnep_set_masses(tnep_ctx* ctx, const double* masses);
+tnep_status tnep_add_com_dipole(tnep_ctx* ctx, int n_structs, const int* atom_offsets, const float* pos,
+                                const float* box, const int* types, const double* charge, double* mu,
+                                int mu_stride, void* stream);
+
 /* Spectrum kinds for tnep_spectrum. */
 enum {
   TNEP_SPECTRUM_IR = 0,          /* series [T][3] = mu(t); omega^2 * lineshape (Eq. 6) */

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -136,6 +137,7 @@ struct tnep_ctx {
   float rc_R = 0.f, rc_A = 0.f;
   std::vector<Model> models;
   std::vector<std::string> type_names;
+  std::vector<double> masses;  // per type (amu), for the centre-of-mass dipole
   Workspace ws;
   PinBuf<double> h_out;
   PinBuf<float> h_stage_f;

@@ -40,6 +40,7 @@ EXPORTED = [
     "tnep_snes_create", "tnep_snes_run", "tnep_snes_state", "tnep_snes_info", "tnep_snes_destroy",
     "tnep_snes_normals", "tnep_snes_update",
     "tnep_raman_tensor", "tnep_raman_polarized", "tnep_raman_porto_map",
+    "tnep_set_masses", "tnep_add_com_dipole",
 ]
 TNEP_NOALLOC_MAX_T = 32768
 
@@ -107,6 +108,8 @@ def _load():
         "tnep_raman_tensor": (C.c_int, [dp, C.c_int, C.c_double, C.c_int, C.c_int, dp, dp, vp]),
         "tnep_raman_polarized": (C.c_int, [dp, C.c_int, C.c_int, dp, dp, dp, vp]),
         "tnep_raman_porto_map": (C.c_int, [dp, C.c_int, C.c_int, dp, C.c_int, dp, dp, vp]),
+        "tnep_set_masses": (C.c_int, [vp, dp]),
+        "tnep_add_com_dipole": (C.c_int, [vp, C.c_int, ip, fp, fp, vp, dp, dp, C.c_int, vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -623,3 +626,22 @@ def tnep_raman_porto_map(L, thetas, axis=2, stream=None):
     _check(_lib.tnep_raman_porto_map(Lb.ptr, M, O, th.ptr, int(axis), par.ctypes.data, crs.ctypes.data,
                                      _stream_ptr(stream)))
     return par, crs
+
+
+def tnep_set_masses(ctx, masses):
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    _check(_lib.tnep_set_masses(ctx.handle, m.ctypes.data))
+
+
+def tnep_add_com_dipole(ctx, offsets, pos, box, types, charge, mu, col=0, stream=None):
+    """mu [S][W] float64 (contiguous, writable; columns col..col+2 hold the
+    dipole, e.g. the output of tnep_eval_batch) gets Q r_COM added in place."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    P = _Buf(pos, np.float32, "pos")
+    B = _Buf(box, np.float32, "box")
+    T = _Buf(types, np.int32, "types")
+    Q = _Buf(charge, np.float64, "charge")
+    M = _Buf(mu, np.float64, "mu", writable=True)
+    _check(_lib.tnep_add_com_dipole(ctx.handle, S, offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, B.ptr, T.ptr,
+                                    Q.ptr, M.ptr + 8 * int(col), int(np.shape(mu)[1]), _stream_ptr(stream)))

@@ -212,6 +212,41 @@ def test_six_type_anions(tn):
     ctx.close()
 
 
+def test_charged_anions_com_dipole(tn):
+    # Sec. III.A: mu = mu_r + Q r_COM for the charged anions, open boxes
+    rng = np.random.default_rng(31)
+    structs = []
+    for n in (25, 44, 58):
+        p, t, b = synth.anion(n, rng)
+        structs.append(synth.Structure((p + rng.uniform(-20, 20, 3)).astype(np.float32), t, b.astype(np.float32)))
+    bt = synth.concat_structures(structs)
+    ms, om = models_for(tn, 6)
+    ctx = tn.tnep_create(ms, 6, RC)
+    masses = np.array([1.008, 12.011, 14.007, 15.999, 18.998, 32.06])  # H C N O F S
+    charge = np.array([-1.0, 0.0, -2.0])
+    with pytest.raises(tn.TnepError):  # masses not set yet
+        tn.tnep_add_com_dipole(ctx, bt.offsets, bt.pos, bt.box, bt.types, charge, np.zeros((3, 3)))
+    tn.tnep_set_masses(ctx, masses)
+    (mu, _), _ = tn.tnep_eval_batch(ctx, bt.offsets, bt.pos, bt.box, bt.types)
+    mu_r = mu.copy()
+    tn.tnep_add_com_dipole(ctx, bt.offsets, bt.pos, bt.box, bt.types, charge, mu)
+    assert np.array_equal(mu[1], mu_r[1])  # neutral structure untouched
+    for s in range(bt.n_structs):
+        a0, a1 = bt.offsets[s], bt.offsets[s + 1]
+        r = oracle.evaluate(om[0], bt.pos[a0:a1], bt.box[s], bt.types[a0:a1])
+        com = oracle.com_dipole(bt.pos[a0:a1], bt.types[a0:a1], masses, charge[s])
+        np.testing.assert_allclose(mu[s] - mu_r[s], com, rtol=1e-12, atol=1e-12 * np.abs(com).max(initial=1.0))
+        ref = r.tensor + com
+        assert np.linalg.norm(mu[s] - ref) <= max(REL * np.linalg.norm(ref), COND * np.abs(r.per_atom).sum())
+    # a charged periodic structure has no centre of mass
+    box = bt.box.copy()
+    box[0] = [30.0, 30.0, 30.0]
+    with pytest.raises(tn.TnepError) as e:
+        tn.tnep_add_com_dipole(ctx, bt.offsets, bt.pos, box, bt.types, charge, mu)
+    assert e.value.status == 1
+    ctx.close()
+
+
 def test_errors_and_neighbor_regrow(tn):
     ms, om = models_for(tn, 2)
     ctx = tn.tnep_create(ms, 2, RC)
