@@ -389,7 +389,7 @@ tnep_status tnep_neighbors(tnep_ctx* c, int n_structs, const int* atom_offsets, 
       oR = tR.p; oA = tA.p; ocR = tcR.p; ocA = tcA.p;
     }
     TNEP_CUDA(launch_export_neighbors(N, c->ws.sorted_orig.p, c->ws.orig_sorted.p, c->ws.nbr_R.p, c->ws.cnt_R.p,
-                                      c->ws.cap_R, c->ws.nbr_A.p, c->ws.cnt_A.p, c->ws.cap_A, ocR, ocA, oR, cap_R,
+                                      c->ws.cap_R, c->ws.seg_R.p, c->ws.two_ended, c->ws.nbr_A.p, c->ws.cnt_A.p, c->ws.cap_A, ocR, ocA, oR, cap_R,
                                       oA, cap_A, st));
     if (!dev) {
       TNEP_CUDA(cudaMemcpyAsync(list_R, tR.p, sizeof(int) * (size_t)N * cap_R, cudaMemcpyDeviceToHost, st));

@@ -200,6 +200,8 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   a.nbr_tmp = w.nbr_tmp.p;
   a.seg_R = w.seg_R.p;
   a.seg_stride = w.atom_stride;
+  w.two_ended = c->n_types == 2 ? 1 : 0;
+  a.two_ended = w.two_ended;
   a.cnt_R = w.cnt_R.p;
   a.cnt_A = w.cnt_A.p;
   a.cap_R = w.cap_R;
@@ -237,6 +239,7 @@ tnep_status skin_lists(tnep_ctx* c, Workspace& w, Workspace& sw, cudaStream_t st
   a.skin_seg = sw.seg_R.p;
   a.skin_cap = sw.cap_R;
   a.skin_seg_stride = sw.atom_stride;
+  a.skin_two_ended = sw.two_ended;
   a.rc2R = c->rc_R * c->rc_R;
   a.rc2A = c->rc_A * c->rc_A;
   const float hs = 0.5f * c->skin * 0.999f;
@@ -253,6 +256,7 @@ tnep_status skin_lists(tnep_ctx* c, Workspace& w, Workspace& sw, cudaStream_t st
   a.cap_R = w.cap_R;
   a.cap_A = w.cap_A;
   a.status = w.d_status;
+  w.two_ended = 0;  // the compacted lists are front-packed per type
   TNEP_CUDA(launch_skin_compact(a, st));
   return TNEP_OK;
 }
@@ -276,6 +280,7 @@ tnep_status compute_moments(tnep_ctx* c, Workspace& w, cudaStream_t st, int N, b
   r.cap_R = w.cap_R;
   r.seg_R = w.seg_R.p;
   r.seg_stride = w.atom_stride;
+  r.two_ended = w.two_ended;
   r.rc_R = c->rc_R;
   r.mom = w.mom.p;
   r.mom_stride = w.atom_stride;

@@ -104,6 +104,7 @@ struct Workspace {
   int atom_stride = 0;
   int cells_cap = 0;
   int cap_R = 0, cap_A = 0;  // caps the lists were built with
+  int two_ended = 0;         // radial list layout of the last build (see NbrArgs)
   void release() {
     for (auto* b : {&offsets, &atom_struct, &atom_cell, &atom_slot, &cell_count, &cell_start, &cell_atoms,
                     &sorted_orig, &orig_sorted, &sorted_struct, &struct_cells, &cnt_R, &cnt_A, &nbr_R, &nbr_A,

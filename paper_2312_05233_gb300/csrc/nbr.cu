@@ -271,6 +271,10 @@ __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL
 // kernel walks one type segment at a time.  (Staging the scratch in shared
 // memory instead was measured slower: it limits the candidate scan to 12
 // warps per SM.)
+// TWO: two atom types, radial entries written straight into their final
+// places (type 0 from entry 0 up, type 1 from entry cap_R - 1 down), with no
+// scratch list and no sort.
+template <bool TWO>
 __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell, float rc2R, float rc2A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_atoms) return;
@@ -296,7 +300,8 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   int* wR = a.nbr_tmp + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
   constexpr int ws = 32;
   int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
-  int cR = 0, cA = 0;
+  int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
+  int cR = 0, cA = 0, c1 = 0;
   for (int iz = 0; iz < nz; ++iz) {
     for (int iy = 0; iy < ny; ++iy) {
       const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
@@ -340,7 +345,16 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
           while (mR) {
             const int j = jb + __ffs(mR) - 1;
             mR &= mR - 1;
-            if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
+            if constexpr (TWO) {
+              if (__float_as_int(a.pos4[j].w) == 0) {
+                if (cR - c1 < a.cap_R) outR[(size_t)(cR - c1) * 32] = j;
+              } else {
+                if (c1 < a.cap_R) outR[(size_t)(a.cap_R - 1 - c1) * 32] = j;
+                ++c1;
+              }
+            } else {
+              if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
+            }
             ++cR;
           }
           while (mA) {
@@ -357,6 +371,11 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   a.cnt_A[i] = cA;
   if (cR > a.cap_R) atomicMax(&a.status->max_cnt_R, cR);
   if (cA > a.cap_A) atomicMax(&a.status->max_cnt_A, cA);
+  if constexpr (TWO) {
+    a.seg_R[i] = cR - c1;
+    a.seg_R[(size_t)a.seg_stride + i] = c1;
+    return;
+  }
   // counting sort of the radial entries by neighbour type; the scratch rows
   // are read eight at a time so that eight loads are in flight per warp
   const int n = min(cR, a.cap_R);
@@ -378,7 +397,6 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   int run = 0;
 #pragma unroll
   for (int u = 0; u < kMaxTypes; ++u) { off[u] = run; run += cnt[u]; }
-  int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
   for (int e0 = 0; e0 < n; e0 += 8) {
     int v[8];
 #pragma unroll
@@ -447,8 +465,9 @@ __global__ void __launch_bounds__(128) k_skin_compact(SkinArgs a) {
   int cR = 0, cA = 0, start = 0;
   for (int t = 0; t < a.n_types; ++t) {
     const int n = a.skin_seg[(size_t)t * a.skin_seg_stride + i];
+    const int e0 = radial_segment_start(a.skin_two_ended, t, start, n, a.skin_cap);
     int kept = 0;
-    for (int e = start; e < start + n; ++e) {
+    for (int e = e0; e < e0 + n; ++e) {
       const int j = a.skin_nbr[nbr_index(i, e, a.skin_cap)];
       const float4 pj = a.pos4[base + j];
       const float dx = mi_diff(pj.x, pi.x, B.L[0], B.invL[0]);
@@ -475,7 +494,7 @@ __global__ void __launch_bounds__(128) k_skin_compact(SkinArgs a) {
 }
 
 __global__ void k_export(int n, const int* sorted_orig, const int* nbr_R, const int* cnt_R, int cap_R,
-                         const int* nbr_A, const int* cnt_A, int cap_A, int* out_cnt_R, int* out_cnt_A,
+                         const int* seg_R, int two_ended, const int* nbr_A, const int* cnt_A, int cap_A, int* out_cnt_R, int* out_cnt_A,
                          int* out_R, int out_cap_R, int* out_A, int out_cap_A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -483,8 +502,12 @@ __global__ void k_export(int n, const int* sorted_orig, const int* nbr_R, const 
   const int nR = cnt_R[i], nA = cnt_A[i];
   out_cnt_R[o] = nR;
   out_cnt_A[o] = nA;
-  for (int k = 0; k < min(nR, min(cap_R, out_cap_R)); ++k)
-    out_R[(size_t)o * out_cap_R + k] = sorted_orig[nbr_R[nbr_index(i, k, cap_R)]];
+  // two-ended lists (nR <= cap_R here): type 1 occupies [cap_R - n1, cap_R)
+  const int n0 = two_ended ? seg_R[i] : nR;
+  for (int k = 0; k < min(nR, min(cap_R, out_cap_R)); ++k) {
+    const int e = k < n0 ? k : cap_R - nR + k;
+    out_R[(size_t)o * out_cap_R + k] = sorted_orig[nbr_R[nbr_index(i, e, cap_R)]];
+  }
   for (int k = 0; k < min(nA, min(cap_A, out_cap_A)); ++k)
     out_A[(size_t)o * out_cap_A + k] = sorted_orig[nbr_A[nbr_index(i, k, cap_A)]];
 }
@@ -506,7 +529,10 @@ cudaError_t launch_neighbor_pipeline(const NbrArgs& a, cudaStream_t st) {
     // sorted_cell reuses atom_slot (dead after the scatter)
     k_cell_sort<<<1216, 256, 0, st>>>(a, a.atom_slot);
     const float rc2R = a.rc_R * a.rc_R, rc2A = a.rc_A * a.rc_A;
-    k_build<<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
+    if (a.two_ended)
+      k_build<true><<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
+    else
+      k_build<false><<<(N + 127) / 128, 128, 0, st>>>(a, a.atom_slot, rc2R, rc2A);
   }
   return cudaGetLastError();
 }
@@ -522,14 +548,15 @@ cudaError_t launch_skin_compact(const SkinArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_export_neighbors(int n_atoms, const int* sorted_orig, const int* orig_sorted,
-                                    const int* nbr_R, const int* cnt_R, int cap_R,
+                                    const int* nbr_R, const int* cnt_R, int cap_R, const int* seg_R, int two_ended,
                                     const int* nbr_A, const int* cnt_A, int cap_A,
                                     int* out_cnt_R, int* out_cnt_A, int* out_R, int out_cap_R,
                                     int* out_A, int out_cap_A, cudaStream_t st) {
   (void)orig_sorted;
   if (n_atoms <= 0) return cudaSuccess;
   count_launches(1);
-  k_export<<<(n_atoms + 127) / 128, 128, 0, st>>>(n_atoms, sorted_orig, nbr_R, cnt_R, cap_R, nbr_A, cnt_A,
+  k_export<<<(n_atoms + 127) / 128, 128, 0, st>>>(n_atoms, sorted_orig, nbr_R, cnt_R, cap_R, seg_R, two_ended,
+                                                   nbr_A, cnt_A,
                                                    cap_A, out_cnt_R, out_cnt_A, out_R, out_cap_R, out_A,
                                                    out_cap_A);
   return cudaGetLastError();

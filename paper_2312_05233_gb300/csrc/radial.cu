@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(128) k_radial(const __grid_constant__ RadialAr
     for (int k = 0; k < (HV ? 3 * B : 1); ++k) V[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < (HW ? 6 * B : 1); ++k) W[k] = 0.f;
-    NbrWalk w(a.nbr_R, a.pos4, i, a.cap_R, start, n, pi);
+    NbrWalk w(a.nbr_R, a.pos4, i, a.cap_R, radial_segment_start(a.two_ended, t, start, n, a.cap_R), n, pi);
     for (int kk = 0; kk < n; ++kk) {
       const float4 pj = w.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
@@ -48,18 +48,24 @@ __global__ void __launch_bounds__(128) k_radial(const __grid_constant__ RadialAr
       const float r = r2 * rinv;
       float f[B], df[B];
       basis_fwd_bwd<B>(r, rcinv, f, df);
+      // pair factors shared by every basis index k
+      float rv[3], rr[6];
+      if constexpr (HV) { rv[0] = r * dx; rv[1] = r * dy; rv[2] = r * dz; }
+      if constexpr (HW) {
+        const float ux = dx * rinv, uy = dy * rinv;
+        rr[0] = ux * dx; rr[1] = ux * dy; rr[2] = ux * dz;
+        rr[3] = uy * dy; rr[4] = uy * dz; rr[5] = dz * rinv * dz;
+      }
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         F[k] += f[k];
         if constexpr (HV) {
-          const float s = r * df[k];
-          V[3 * k] += s * dx; V[3 * k + 1] += s * dy; V[3 * k + 2] += s * dz;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) V[3 * k + c] = fmaf(df[k], rv[c], V[3 * k + c]);
         }
         if constexpr (HW) {
-          const float s = df[k] * rinv;
-          const float sx = s * dx, sy = s * dy;
-          W[6 * k] += sx * dx; W[6 * k + 1] += sx * dy; W[6 * k + 2] += sx * dz;
-          W[6 * k + 3] += sy * dy; W[6 * k + 4] += sy * dz; W[6 * k + 5] += s * dz * dz;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) W[6 * k + c] = fmaf(df[k], rr[c], W[6 * k + c]);
         }
       }
     }

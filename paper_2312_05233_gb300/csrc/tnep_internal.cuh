@@ -80,11 +80,18 @@ struct NbrArgs {
   int* nbr_tmp;             // radial scratch (type-tagged), same layout as nbr_R
   int* seg_R;               // [n_types][seg_stride] radial neighbours of each type
   int seg_stride;
+  int two_ended;            // two types: type 0 from entry 0 up, type 1 from entry cap_R - 1 down
   int* cnt_R; int* cnt_A;   // [N] true counts (may exceed caps)
   int cap_R, cap_A;
   int cells_cap;
   DevStatus* status;
 };
+
+// First radial-list entry of neighbour type t: the running start of the
+// front-packed layout, or cap - n for type 1 of a two-ended list.
+__host__ __device__ inline int radial_segment_start(int two_ended, int t, int running, int n, int cap) {
+  return (two_ended && t == 1) ? cap - n : running;
+}
 
 // Sets the thread-local message returned by tnep_last_error().
 void set_last_error(const char* msg);
@@ -104,6 +111,7 @@ struct SkinArgs {
   const float4* ref4;         // first frame positions, sorted
   const StructBox* ref_box;   // first frame box
   const int* skin_nbr; const int* skin_seg; int skin_cap, skin_seg_stride;  // type-sorted skin lists
+  int skin_two_ended;
   float rc2R, rc2A, half_skin2;
   float4* pos4; int* sorted_struct; StructBox* boxes;   // batch outputs
   int* nbr_R; int* nbr_A; int* cnt_R; int* cnt_A; int* seg_R; int seg_stride; int cap_R, cap_A;
@@ -127,6 +135,7 @@ struct RadialArgs {
   const StructBox* boxes;
   const int* nbr_R; int cap_R;
   const int* seg_R; int seg_stride;
+  int two_ended;
   float rc_R;
   float* mom; int mom_stride;
   int v0, w0;  // slot bases, -1 when not computed
@@ -184,7 +193,7 @@ cudaError_t launch_gather_per_atom(int n_atoms, const int* orig_sorted, const fl
 
 // Converts warp-tiled sorted-index lists to row-major input-order lists.
 cudaError_t launch_export_neighbors(int n_atoms, const int* sorted_orig, const int* orig_sorted,
-                                    const int* nbr_R, const int* cnt_R, int cap_R,
+                                    const int* nbr_R, const int* cnt_R, int cap_R, const int* seg_R, int two_ended,
                                     const int* nbr_A, const int* cnt_A, int cap_A,
                                     int* out_cnt_R, int* out_cnt_A, int* out_R, int out_cap_R,
                                     int* out_A, int out_cap_A, cudaStream_t st);
