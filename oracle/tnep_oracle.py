@@ -73,7 +73,7 @@ WAVENUMBER_PER_INV_FS = 1.0 / 2.99792458e-5  # 1 fs^-1 in cm^-1
 __all__ = [
     "OracleModel", "pairs_fp64", "neighbours_fp32", "wigner3j",
     "sph_harm_complex", "evaluate", "evaluate_frames", "site_energies_from_pairs",
-    "acf", "spectrum", "KIND_IR", "KIND_RAMAN_ISO", "KIND_RAMAN_ANISO", "com_dipole",
+    "acf", "spectrum", "KIND_IR", "KIND_RAMAN_ISO", "KIND_RAMAN_ANISO", "com_dipole", "pairs_cell",
 ]
 
 KIND_IR, KIND_RAMAN_ISO, KIND_RAMAN_ANISO = 0, 1, 2
@@ -184,6 +184,44 @@ def pairs_fp64(pos, box, rc, centers=None):
     if not I:
         return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros((0, 3))
     return np.concatenate(I), np.concatenate(J), np.concatenate(R)
+
+
+def pairs_cell(pos, cell, rc, centers=None):
+    """Pairs under a general periodic cell (rows of ``cell`` are the lattice
+    vectors a, b, c; r = s H for fractional s): every (i, j, n) with
+    |r_j + n H - r_i| < rc and (j, n) != (i, 0), so a neighbour appears once
+    per image within the cutoff (cells of any shape, also shorter than twice
+    the cutoff).  Positions are first wrapped into the cell; the images are
+    enumerated by brute force over n in [-k, k]^3 with k_a = ceil(rc / d_a) + 1,
+    d_a the spacing of the lattice planes normal to axis a.  Returns
+    (i, j, r_ij) with r_ij = r_j + n H - r_i, sorted by i, then j, then n.
+    """
+    H = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    vol = abs(np.linalg.det(H))
+    if vol <= 0:
+        raise ValueError("degenerate cell")
+    s = np.asarray(pos, dtype=np.float64) @ np.linalg.inv(H)
+    r = (s - np.floor(s)) @ H
+    n_at = len(r)
+    centers = np.arange(n_at) if centers is None else np.asarray(centers)
+    spacing = [vol / np.linalg.norm(np.cross(H[(a + 1) % 3], H[(a + 2) % 3])) for a in range(3)]
+    k = [int(np.ceil(rc / d)) + 1 for d in spacing]
+    I, J, N, R = [], [], [], []
+    for n0 in range(-k[0], k[0] + 1):
+        for n1 in range(-k[1], k[1] + 1):
+            for n2 in range(-k[2], k[2] + 1):
+                shift = np.array([n0, n1, n2], dtype=np.float64) @ H
+                d = r[None, :, :] + shift - r[centers][:, None, :]
+                r2 = np.einsum("cja,cja->cj", d, d)
+                mask = r2 < rc * rc
+                if n0 == 0 and n1 == 0 and n2 == 0:
+                    mask[np.arange(len(centers)), centers] = False
+                ci, jj = np.nonzero(mask)
+                nid = ((n0 + k[0]) * (2 * k[1] + 1) + (n1 + k[1])) * (2 * k[2] + 1) + (n2 + k[2])
+                I.append(centers[ci]); J.append(jj); N.append(np.full(len(ci), nid)); R.append(d[ci, jj])
+    I, J, N, R = (np.concatenate(x) for x in (I, J, N, R))
+    order = np.lexsort((N, J, I))
+    return I[order], J[order], R[order]
 
 
 def neighbours_fp32(pos, box, rc):
@@ -420,12 +458,18 @@ class OracleResult:
     virial: np.ndarray     # [9] (Eq. 2)
 
 
-def evaluate(m: OracleModel, pos, box, types, centers=None, mode="factorized") -> OracleResult:
-    """One structure.  ``centers`` restricts the sum over i to a subset."""
+def evaluate(m: OracleModel, pos, box, types, centers=None, mode="factorized", cell=None) -> OracleResult:
+    """One structure.  ``centers`` restricts the sum over i to a subset.
+    With ``cell`` (3x3, rows = lattice vectors) the structure is periodic in
+    that cell with every image within the cutoff (see pairs_cell) and
+    ``box`` is ignored."""
     pos = np.asarray(pos, dtype=np.float64)
     box = np.zeros(3) if box is None else np.asarray(box, dtype=np.float64)
     n = len(pos)
-    i, j, R = pairs_fp64(pos, box, m.rc_R, centers)
+    if cell is not None:
+        i, j, R = pairs_cell(pos, cell, m.rc_R, centers)
+    else:
+        i, j, R = pairs_fp64(pos, box, m.rc_R, centers)
     rij = torch.tensor(R, dtype=DT, requires_grad=True)
     U, q = site_energies_from_pairs(m, n, types, i, j, rij, mode)
     cmask = np.zeros(n, bool)

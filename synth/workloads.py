@@ -37,7 +37,7 @@ __all__ = [
     "bzo_supercell", "thermal_frames", "water_cluster", "anion",
     "poisson_arrivals", "Structure", "StructureBatch", "concat_structures",
     "water_small", "water_bulk", "bzo_perovskite", "population_structures",
-    "serving_requests", "snes_update_inputs", "tensor_targets", "tensor_series",
+    "serving_requests", "snes_update_inputs", "tensor_targets", "tensor_series", "cell_water",
 ]
 
 
@@ -375,3 +375,32 @@ def tensor_series(n_steps: int, rng: np.random.Generator, n_modes: int = 4, dt_f
     if symmetric:
         out = 0.5 * (out + out.transpose(0, 2, 1))
     return out.reshape(n_steps, 9)
+
+
+def cell_water(n_mol: int, cell: np.ndarray, rng: np.random.Generator, min_dist: float = 2.6):
+    """Water molecules at random positions inside a general cell (rows =
+    lattice vectors), oxygens at least min_dist apart under every image;
+    returns (pos [3 n_mol][3], types, cell)."""
+    H = np.asarray(cell, dtype=np.float64)
+    centres = []
+    tries = 0
+    while len(centres) < n_mol:
+        tries += 1
+        if tries > 200000:
+            raise RuntimeError("cell too small for the requested molecules")
+        c = rng.uniform(0.0, 1.0, 3) @ H
+        ok = True
+        for o in centres:
+            d = (c - o) @ np.linalg.inv(H)
+            d -= np.round(d)
+            for sh in np.array(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1])).T.reshape(-1, 3):
+                if np.linalg.norm((d + sh) @ H) < min_dist:
+                    ok = False
+                    break
+            if not ok:
+                break
+        if ok:
+            centres.append(c)
+    pos = _place_waters(np.array(centres), rng)
+    types = np.tile(np.array([0, 1, 1], dtype=np.int32), n_mol)
+    return pos, types, H

@@ -366,3 +366,80 @@ def test_com_dipole_closed_forms():
     np.testing.assert_allclose(oracle.com_dipole(pos, np.zeros(7, int), masses, 1.0), pos.mean(0), atol=1e-14)
     # only mass ratios matter
     np.testing.assert_allclose(oracle.com_dipole(pos, types, 3.7 * masses, q), base, atol=1e-13)
+
+
+# ----------------------------------------------------------------- general periodic cells
+def test_cell_pairs_equal_minimum_image_for_large_orthorhombic_cells():
+    rng = np.random.default_rng(40)
+    pos, types, box = synth.water_box(64, rng, L=12.42)
+    i0, j0, r0 = pairs_fp64(pos, box, RC_R)
+    i1, j1, r1 = oracle.pairs_cell(pos, np.diag(box), RC_R)
+    o0, o1 = np.lexsort((j0, i0)), np.lexsort((j1, i1))
+    assert np.array_equal(i0[o0], i1[o1]) and np.array_equal(j0[o0], j1[o1])
+    np.testing.assert_allclose(r0[o0], r1[o1], atol=1e-12)
+
+
+@pytest.mark.parametrize("rank,L,n_mol,reps", [(1, 9.0, 24, 2), (2, 9.0, 24, 2), (2, 5.0, 3, 3)])
+def test_small_cell_equals_its_supercell(rank, L, n_mol, reps):
+    # cells shorter than 2 rc (the 5 A cube even shorter than rc: an atom sees
+    # its own images): every image within the cutoff counts; the supercell of
+    # edge >= 2 rc uses the plain minimum image instead
+    _, _, m = make_model(rank=rank)
+    rng = np.random.default_rng(41)
+    pos, types, box = synth.water_box(n_mol, rng, L=L)
+    small = oracle.evaluate(m, pos, None, types, cell=np.diag(box))
+    shifts = [np.array([a, b, c]) for a in range(reps) for b in range(reps) for c in range(reps)]
+    big_pos = np.concatenate([pos + L * sh for sh in shifts])
+    big = oracle.evaluate(m, big_pos, np.full(3, reps * L), np.tile(types, len(shifts)))
+    np.testing.assert_allclose(big.per_atom[:len(types)], small.per_atom, atol=1e-10 * np.abs(small.per_atom).max())
+    np.testing.assert_allclose(big.tensor, len(shifts) * small.tensor, atol=1e-10 * np.abs(big.per_atom).sum())
+
+
+def _sheared_cell():
+    return np.array([[8.0, 0.0, 0.0], [2.5, 7.5, 0.0], [-1.5, 2.0, 8.5]])
+
+
+def test_triclinic_cell_basis_change_and_supercell():
+    _, _, m = make_model(rank=2)
+    H = _sheared_cell()
+    pos, types, _ = synth.cell_water(14, H, np.random.default_rng(42))
+    ref = oracle.evaluate(m, pos, None, types, cell=H)
+    # the same lattice in another basis (unimodular integer change)
+    M = np.array([[1, 1, 0], [0, 1, 0], [1, 0, 1]])
+    alt = oracle.evaluate(m, pos, None, types, cell=M @ H)
+    np.testing.assert_allclose(alt.per_atom, ref.per_atom, atol=1e-10 * np.abs(ref.per_atom).max())
+    # 2x1x1 supercell along a: every atom keeps its contribution
+    big_pos = np.concatenate([pos, pos + H[0]])
+    big = oracle.evaluate(m, big_pos, None, np.tile(types, 2), cell=np.diag([2, 1, 1]) @ H)
+    np.testing.assert_allclose(big.per_atom[:len(types)], ref.per_atom, atol=1e-10 * np.abs(ref.per_atom).max())
+    np.testing.assert_allclose(big.per_atom[len(types):], ref.per_atom, atol=1e-10 * np.abs(ref.per_atom).max())
+
+
+def test_triclinic_cell_rotates_with_the_structure():
+    _, _, m1 = make_model(rank=1)
+    _, _, m2 = make_model(rank=2)
+    H = _sheared_cell()
+    pos, types, _ = synth.cell_water(12, H, np.random.default_rng(43))
+    R = synth.random_rotation(np.random.default_rng(44))
+    for m in (m1, m2):
+        a = oracle.evaluate(m, pos, None, types, cell=H).tensor
+        b = oracle.evaluate(m, pos @ R.T, None, types, cell=H @ R.T).tensor
+        if m.rank == 1:
+            np.testing.assert_allclose(b, R @ a, atol=1e-10 * np.abs(a).max())
+        else:
+            np.testing.assert_allclose(b.reshape(3, 3), R @ a.reshape(3, 3) @ R.T, atol=1e-10 * np.abs(a).max())
+
+
+def test_lattice_translations_of_single_atoms_change_nothing():
+    # moving atoms by whole lattice vectors (far outside the cell) is no change;
+    # a strongly sheared cell, whose plane spacings are well below its edges
+    _, _, m = make_model(rank=2)
+    H = np.array([[7.0, 0.0, 0.0], [5.5, 6.5, 0.0], [4.0, -3.0, 7.5]])
+    pos, types, _ = synth.cell_water(10, H, np.random.default_rng(45))
+    ref = oracle.evaluate(m, pos, None, types, cell=H)
+    moved = pos.copy()
+    moved[3] += 3 * H[0] - 2 * H[2]
+    moved[10] -= 4 * H[1]
+    moved[17] += H[0] + H[1] + H[2]
+    got = oracle.evaluate(m, moved, None, types, cell=H)
+    np.testing.assert_allclose(got.per_atom, ref.per_atom, atol=1e-10 * np.abs(ref.per_atom).max())
