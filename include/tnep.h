@@ -149,6 +149,26 @@ tnep_status tnep_eval_batch(tnep_ctx* ctx, int n_structs, const int* atom_offset
                             const float* pos, const float* box, const int* types,
                             double* out, float* per_atom, void* stream);
 
+/* General periodic cells (Sec. II.A): triclinic cells, and cells shorter
+ * than twice the cutoff.  U_i depends on the pair vectors to every neighbour
+ * within the cutoff, so here a neighbour counts once per image
+ * r_j + n H (n integer) within the cutoff -- in a small cell an atom can see
+ * another one, or itself, several times.
+ *   cell [n_structs][9] float32: rows a, b, c of H (A), row-major; a
+ *        structure whose nine entries are all 0 is open; NULL = all open
+ *   pos  [N][3] anywhere in space (atoms are wrapped into the cell first)
+ *   out  [n_models][n_structs][C_m] float64, as tnep_eval_batch
+ * Each periodic structure is expanded on the device into its wrapped atoms
+ * plus every image within rc_R / d_a of the cell in fractional coordinates
+ * (d_a the lattice-plane spacings), and evaluated as an open structure with
+ * the images left out of the sums: the cost grows about as
+ * (1 + 2 rc_R / d)^3 for a cell of spacing d.  Host or device buffers
+ * (atom_offsets host).  Synchronous.
+ * Errors: INVALID (degenerate cell |det H| <= 1e-9, bad sizes or types, more
+ * than 2^29 atoms after expansion), NEIGHBOR_OVERFLOW, OOM, CUDA. */
+tnep_status tnep_eval_batch_cell(tnep_ctx* ctx, int n_structs, const int* atom_offsets, const float* pos,
+                                 const float* cell, const int* types, double* out, void* stream);
+
 /* Builds the neighbour lists of a batch (the cell-list and pair-selection
  * steps of the path) and returns them in input atom order for inspection.
  *   counts_R/counts_A [N]: neighbours within rc_R / rc_A
@@ -259,8 +279,9 @@ tnep_status tnep_snes_update(int n_pop, int dim, const double* loss, const doubl
  *     mu = mu_r + Q r_COM,   r_COM = sum_i m_i r_i / sum_i m_i.
  * tnep_set_masses stores one mass per type (any unit; only ratios matter).
  * tnep_add_com_dipole adds Q_s r_COM,s to mu[s * mu_stride + 0..2] in place for
- * each structure s of a batch (layout of tnep_eval_batch: pass
- * out + column offset of the rank-1 model and mu_stride = total width).
+ * each structure s of a batch (for the output of tnep_eval_batch, whose
+ * layout is [n_models][n_structs][C_m], pass the rank-1 model's block and
+ * mu_stride = 3).
  *   charge [n_structs] float64 in e (0 = neutral, left unchanged); a charged
  *   structure must be open (box row 0 0 0, checked for host buffers).
  *   atom_offsets host; pos, box (may be NULL = all open), types, charge, mu

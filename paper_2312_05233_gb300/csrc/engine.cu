@@ -353,7 +353,8 @@ tnep_status sum_pass_times(tnep_ctx* c, int n_pass) {
   return TNEP_OK;
 }
 
-tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done) {
+tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done,
+                       const unsigned char* ghost) {
   const size_t per_model = (size_t)9 * w.atom_stride;
   TNEP_CUDA(w.per_atom.ensure(per_model * c->models.size()));
   TNEP_CUDA(w.out.ensure((size_t)std::max(S, 1) * total_C(c)));
@@ -366,6 +367,10 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
     TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, m.d.mlp_precision, st));
   }
   if (ev_done) TNEP_CUDA(cudaEventRecord(ev_done, st));
+  if (ghost)
+    for (size_t k = 0; k < c->models.size(); ++k)
+      TNEP_CUDA(launch_zero_ghosts(N, w.sorted_orig.p, ghost, w.per_atom.p + k * per_model, w.atom_stride,
+                                   c->models[k].C, st));
   TNEP_CUDA(w.partial.ensure((size_t)std::max(S, 1) * reduce_chunks(w.max_atoms) * 9));
   size_t off = 0;
   for (size_t k = 0; k < c->models.size(); ++k) {

@@ -184,7 +184,12 @@ FusedArgs fused_args(tnep_ctx* c, Workspace& w, const Model& m, int N);
 int total_C(const tnep_ctx* c);
 tnep_status pass_events(tnep_ctx* c, int b, cudaEvent_t** ev);
 tnep_status sum_pass_times(tnep_ctx* c, int n_pass);
-tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done);
+// ghost: NULL, or one flag per atom of the batch (input order) marking image
+// atoms whose contributions are left out of the per-structure sums.
+tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done,
+                       const unsigned char* ghost = nullptr);
+cudaError_t launch_zero_ghosts(int N, const int* sorted_orig, const unsigned char* ghost, float* per_atom,
+                               int atom_stride, int C, cudaStream_t st);
 tnep_status check_status(tnep_ctx* c, const DevStatus& s, bool* regrow);
 tnep_status reset_status(Workspace& w, cudaStream_t st);
 tnep_status finish(tnep_ctx* c, Workspace& w, cudaStream_t st, bool* regrow);

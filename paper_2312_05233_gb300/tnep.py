@@ -40,7 +40,7 @@ EXPORTED = [
     "tnep_snes_create", "tnep_snes_run", "tnep_snes_state", "tnep_snes_info", "tnep_snes_destroy",
     "tnep_snes_normals", "tnep_snes_update",
     "tnep_raman_tensor", "tnep_raman_polarized", "tnep_raman_porto_map",
-    "tnep_set_masses", "tnep_add_com_dipole",
+    "tnep_set_masses", "tnep_add_com_dipole", "tnep_eval_batch_cell",
 ]
 TNEP_NOALLOC_MAX_T = 32768
 
@@ -110,6 +110,7 @@ def _load():
         "tnep_raman_porto_map": (C.c_int, [dp, C.c_int, C.c_int, dp, C.c_int, dp, dp, vp]),
         "tnep_set_masses": (C.c_int, [vp, dp]),
         "tnep_add_com_dipole": (C.c_int, [vp, C.c_int, ip, fp, fp, vp, dp, dp, C.c_int, vp]),
+        "tnep_eval_batch_cell": (C.c_int, [vp, C.c_int, ip, fp, fp, vp, dp, vp]),
         "tnep_set_option": (C.c_int, [vp, C.c_int, C.c_double]),
         "tnep_get_option": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double)]),
     }
@@ -327,6 +328,26 @@ def tnep_eval_batch(ctx: Context, offsets, pos, box, types, per_atom=False, out=
             pres.append(pa[poff:poff + N * c].reshape(N, c))
             poff += N * c
     return res, (pres if per_atom else None)
+
+
+def tnep_eval_batch_cell(ctx: Context, offsets, pos, cell, types, stream=None):
+    """General periodic cells: cell [S][3][3] (rows = lattice vectors, zeros = open) or None.
+
+    Returns a list of [S][C_m] arrays, one per model."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    S = len(offs) - 1
+    P = _Buf(pos, np.float32, "pos")
+    H = _Buf(None if cell is None else np.asarray(cell, dtype=np.float32).reshape(S, 9), np.float32, "cell")
+    T = _Buf(types, np.int32, "types")
+    tot = sum(ctx.dims)
+    out = np.zeros(S * tot)
+    _check(_lib.tnep_eval_batch_cell(ctx.handle, S, offs.ctypes.data_as(C.POINTER(C.c_int)), P.ptr, H.ptr, T.ptr,
+                                     out.ctypes.data, _stream_ptr(stream)))
+    res, off = [], 0
+    for c in ctx.dims:
+        res.append(out[off:off + S * c].reshape(S, c))
+        off += S * c
+    return res
 
 
 def tnep_neighbors(ctx: Context, offsets, pos, box, cap_R=256, cap_A=128, stream=None):
