@@ -259,7 +259,8 @@ def population_bench(tn, synth, device, n_pop=50, gens=5):
     return {"workload": f"{n_pop} parameter vectors x {bt.n_structs} structures ({atoms} atoms), rank 1",
             "generation_ms": wall * 1e3, "generation_device_ms": dev_ms / gens,
             "atom_evals_per_s": n_pop * atoms / wall, "oneshot_ms": oneshot * 1e3,
-            "chosen": {"atoms_per_cta": info["block"], "individual_major": info["pop_major"]},
+            "chosen": {"atoms_per_cta": info["block"], "individual_major": info["pop_major"],
+                       "factored": info["factored"]},
             "candidates_ms": info["tune_ms"], "rmse_first": float(rmse[0])}
 
 

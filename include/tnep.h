@@ -208,11 +208,13 @@ tnep_status tnep_population_create(tnep_ctx* ctx, int model, int n_pop, const fl
 /* Replays the captured generation for new parameters [n_pop][n_params] (host):
  * rmse [n_pop], out NULL or [n_pop][n_structs][C] (host).  Synchronous. */
 tnep_status tnep_population_eval(tnep_population* pop, const float* params, double* rmse, double* out);
-/* info[8]: atoms per CTA and CTA order chosen, the four timed candidates (ms per
- * generation: 128/atom-major, 128/individual-major, 64/atom-major,
- * 64/individual-major; -1 = not applicable), last generation's device time (ms),
- * atoms in the structure set. */
-tnep_status tnep_population_info(const tnep_population* pop, double info[8]);
+/* info[13]: atoms per CTA, CTA order and form chosen (0 = per-pair angular
+ * walk, 1 = factored through the angular moments), the eight timed candidates
+ * (ms per generation: walk with 128/atom-major, 128/individual-major,
+ * 64/atom-major, 64/individual-major, then the factored form in the same
+ * order; -1 = not applicable), last generation's device time (ms), atoms in
+ * the structure set. */
+tnep_status tnep_population_info(const tnep_population* pop, double info[13]);
 void tnep_population_destroy(tnep_population* pop);
 
 /* ---- Training loop: separable natural evolution strategy (Sec. II.D) ----
@@ -421,7 +423,10 @@ enum {
                                        moved more than s / 2 within a pass, or the box changed, the call redoes
                                        every pass with lists built per frame.  Results agree with s = 0 to float32
                                        rounding (pair order may differ). */
-  TNEP_OPT_LAST_SKIN_USED = 9       /* read-only: 1 if the last tnep_eval used skin lists in every pass */
+  TNEP_OPT_LAST_SKIN_USED = 9,      /* read-only: 1 if the last tnep_eval used skin lists in every pass */
+  TNEP_OPT_POPULATION_FORM = 10     /* angular form of populations created afterwards: 0 = the faster of the
+                                       two by timing (default), 1 = per-pair walk, 2 = factored through the
+                                       angular moments (FP32 network only; otherwise the walk) */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

@@ -156,6 +156,10 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       if (!(value >= 0.0) || value > 2.0) return fail(TNEP_ERR_INVALID, "skin must be in [0, 2] Angstrom");
       c->skin = (float)value;
       return TNEP_OK;
+    case TNEP_OPT_POPULATION_FORM:
+      if (value != 0.0 && value != 1.0 && value != 2.0) return fail(TNEP_ERR_INVALID, "population form must be 0, 1 or 2");
+      c->population_form = (int)value;
+      return TNEP_OK;
     default:
       return fail(TNEP_ERR_INVALID, "unknown or read-only option");
   }
@@ -173,6 +177,7 @@ tnep_status tnep_get_option(const tnep_ctx* c, int option, double* value) {
     case TNEP_OPT_LAST_NBR_MS: *value = c->last_nbr_ms; return TNEP_OK;
     case TNEP_OPT_KERNEL_LAUNCHES_TOTAL: *value = (double)launches_total(); return TNEP_OK;
     case TNEP_OPT_SKIN: *value = c->skin; return TNEP_OK;
+    case TNEP_OPT_POPULATION_FORM: *value = c->population_form; return TNEP_OK;
     case TNEP_OPT_LAST_SKIN_USED: *value = c->last_skin_used; return TNEP_OK;
     default: return fail(TNEP_ERR_INVALID, "unknown option");
   }

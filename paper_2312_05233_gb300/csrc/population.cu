@@ -2,14 +2,17 @@
 // natural evolution strategy evaluates a population of parameter vectors on
 // the training structures every generation).
 //
-// The neighbour lists and the radial moments depend only on the structures,
-// so tnep_population_create builds them once.  The per-generation work --
+// The neighbour lists, the radial moments and the angular moments (g_n is
+// linear in the coefficients that differ between individuals; angmom.cu)
+// depend only on the structures, so tnep_population_create builds them once.  The per-generation work --
 // upload of the packed parameter vectors, one fused-kernel launch over all
 // individuals x atoms, the FP64 per-structure reduction, the RMSE per
 // individual and the read-back -- is captured once into a CUDA graph and
 // replayed by tnep_population_eval.  The launch shape (atoms per CTA, and
 // whether consecutive CTAs vary the individual or the atom block) is picked
-// by timing the candidates on the actual structures.
+// by timing the candidates on the actual structures, together with the choice
+// between the per-pair angular walk and the factored form through the angular
+// moments.
 
 #include <cuda_runtime.h>
 
@@ -36,8 +39,10 @@ struct tnep_population {
   PinBuf<double> h_rmse, h_pred;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int block = 128, pop_major = 0;
-  double tune_ms[4] = {0, 0, 0, 0};
+  int block = 128, pop_major = 0, fact = 0;
+  bool fact_ok = false;          // angular moments available
+  DevBuf<float> amom;            // angular moments (factored form)
+  double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double last_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -52,6 +57,10 @@ FusedArgs pop_args(tnep_population* p) {
   f.per_atom = p->ws.per_atom.p;
   f.per_atom_stride = (size_t)m.C * p->ws.atom_stride;
   f.pop_major = p->pop_major;
+  if (p->fact) {
+    f.amom = p->amom.p;
+    f.amom_stride = p->ws.atom_stride;
+  }
   return f;
 }
 
@@ -83,34 +92,44 @@ tnep_status pack_all(tnep_population* p, const float* params) {
   return TNEP_OK;
 }
 
-// Times the fused launch for each candidate shape and keeps the fastest.
+// Times the fused launch for each candidate shape (and, where the angular
+// moments exist, the factored form) and keeps the fastest.
 tnep_status autotune(tnep_population* p) {
   const int blocks[2] = {128, 64};
   double best = 1e30;
-  int best_b = 128, best_o = 0, idx = 0;
+  int best_b = 128, best_o = 0, best_f = 0, idx = 0;
   TNEP_CUDA(cudaMemcpyAsync(p->d_params.p, p->h_params.p,
                             sizeof(float) * (size_t)p->n_pop * p->ctx->models[p->model].lay.words,
                             cudaMemcpyHostToDevice, p->stream));
-  for (int b : blocks) {
-    for (int order = 0; order < 2; ++order, ++idx) {
-      p->block = b;
-      p->pop_major = order;
-      const int nblk = (p->N + b - 1) / b;
-      const bool tc = p->ctx->models[p->model].d.mlp_precision != 0;
-      if ((order == 1 && nblk > 65535) || (tc && b != 128)) { p->tune_ms[idx] = -1; continue; }
-      TNEP_TRY(enqueue_generation(p, false));  // warm-up
-      TNEP_CUDA(cudaEventRecord(p->ev0, p->stream));
-      for (int r = 0; r < 3; ++r) TNEP_TRY(enqueue_generation(p, false));
-      TNEP_CUDA(cudaEventRecord(p->ev1, p->stream));
-      TNEP_CUDA(cudaEventSynchronize(p->ev1));
-      float ms = 0.f;
-      TNEP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
-      p->tune_ms[idx] = ms / 3.0;
-      if (ms < best) { best = ms; best_b = b; best_o = order; }
+  for (int fact = 0; fact < 2; ++fact) {
+    for (int b : blocks) {
+      for (int order = 0; order < 2; ++order, ++idx) {
+        p->block = b;
+        p->pop_major = order;
+        p->fact = fact;
+        const int nblk = (p->N + b - 1) / b;
+        const bool tc = p->ctx->models[p->model].d.mlp_precision != 0;
+        const int form = p->ctx->population_form;
+        if ((order == 1 && nblk > 65535) || (tc && b != 128) || (fact && !p->fact_ok) ||
+            (form == 1 && fact) || (form == 2 && p->fact_ok && !fact)) {
+          p->tune_ms[idx] = -1;
+          continue;
+        }
+        TNEP_TRY(enqueue_generation(p, false));  // warm-up
+        TNEP_CUDA(cudaEventRecord(p->ev0, p->stream));
+        for (int r = 0; r < 3; ++r) TNEP_TRY(enqueue_generation(p, false));
+        TNEP_CUDA(cudaEventRecord(p->ev1, p->stream));
+        TNEP_CUDA(cudaEventSynchronize(p->ev1));
+        float ms = 0.f;
+        TNEP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->tune_ms[idx] = ms / 3.0;
+        if (ms < best) { best = ms; best_b = b; best_o = order; best_f = fact; }
+      }
     }
   }
   p->block = best_b;
   p->pop_major = best_o;
+  p->fact = best_f;
   return TNEP_OK;
 }
 
@@ -125,6 +144,7 @@ void destroy_pop(tnep_population* p) {
   p->ws.release();
   p->d_pos.release(); p->d_box.release(); p->d_types.release(); p->d_params.release(); p->h_params.release();
   p->d_target.release(); p->d_rmse.release(); p->d_pred.release(); p->h_rmse.release(); p->h_pred.release();
+  p->amom.release();
   if (p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -162,6 +182,30 @@ tnep_status create_pop(tnep_population* p, const float* params0, const float* po
     if (!regrow) break;
   }
   TNEP_TRY(compute_moments(c, p->ws, st, N, m.d.rank == 1, m.d.rank == 2));
+  // angular moments for the factored form (FP32 network only); without the
+  // memory for them the per-pair walk is used
+  if (m.d.mlp_precision == 0 && N > 0) {
+    const size_t slots = angular_moment_slots(m.variant, m.d.rank, c->n_types);
+    if (p->amom.ensure(slots * p->ws.atom_stride) == cudaSuccess) {
+      AngMomArgs am{};
+      am.n_atoms = N;
+      am.n_types = c->n_types;
+      am.pos4 = p->ws.pos4.p;
+      am.sorted_struct = p->ws.sorted_struct.p;
+      am.boxes = p->ws.boxes.p;
+      am.nbr_A = p->ws.nbr_A.p;
+      am.cnt_A = p->ws.cnt_A.p;
+      am.cap_A = p->ws.cap_A;
+      am.rc_A = c->rc_A;
+      am.amom = p->amom.p;
+      am.amom_stride = p->ws.atom_stride;
+      TNEP_CUDA(launch_angular_moments(m.variant, m.d.rank, am, st));
+      p->fact_ok = true;
+    } else {
+      cudaGetLastError();
+      p->amom.release();
+    }
+  }
   const size_t pa = (size_t)m.C * p->ws.atom_stride * p->n_pop;
   TNEP_CUDA(p->ws.per_atom.ensure(pa));
   TNEP_CUDA(p->ws.partial.ensure((size_t)p->n_pop * S * reduce_chunks(p->ws.max_atoms) * m.C));
@@ -250,13 +294,14 @@ tnep_status tnep_population_eval(tnep_population* p, const float* params, double
   return TNEP_OK;
 }
 
-tnep_status tnep_population_info(const tnep_population* p, double info[8]) {
+tnep_status tnep_population_info(const tnep_population* p, double info[13]) {
   if (!p || !info) return fail(TNEP_ERR_INVALID, "NULL argument");
   info[0] = p->block;
   info[1] = p->pop_major;
-  for (int k = 0; k < 4; ++k) info[2 + k] = p->tune_ms[k];
-  info[6] = p->last_ms;
-  info[7] = p->N;
+  info[2] = p->fact;
+  for (int k = 0; k < 8; ++k) info[3 + k] = p->tune_ms[k];
+  info[11] = p->last_ms;
+  info[12] = p->N;
   return TNEP_OK;
 }
 

@@ -95,4 +95,82 @@ struct NbrWalk {
   }
 };
 
+// Real polynomials p_lm(x, y, z) on the unit sphere:
+// l=1: x, y, z
+// l=2: xy, yz, xz, x^2-y^2, 3z^2-1
+// l=3: y(3x^2-y^2), xyz, y(5z^2-1), z(5z^2-3), x(5z^2-1), z(x^2-y^2), x(x^2-3y^2)
+// l=4: xy(x^2-y^2), yz(3x^2-y^2), xy(7z^2-1), yz(7z^2-3), 35z^4-30z^2+3,
+//      xz(7z^2-3), (x^2-y^2)(7z^2-1), xz(x^2-3y^2), x^4-6x^2y^2+y^4
+template <int LMAX>
+__device__ __forceinline__ void real_harmonics(float x, float y, float z, float* p) {
+  p[0] = x; p[1] = y; p[2] = z;
+  if constexpr (LMAX >= 2) {
+    const float x2 = x * x, y2 = y * y, z2 = z * z;
+    p[3] = x * y; p[4] = y * z; p[5] = x * z; p[6] = x2 - y2; p[7] = 3.f * z2 - 1.f;
+    if constexpr (LMAX >= 3) {
+      const float t5 = 5.f * z2;
+      p[8] = y * (3.f * x2 - y2);
+      p[9] = x * y * z;
+      p[10] = y * (t5 - 1.f);
+      p[11] = z * (t5 - 3.f);
+      p[12] = x * (t5 - 1.f);
+      p[13] = z * (x2 - y2);
+      p[14] = x * (x2 - 3.f * y2);
+      if constexpr (LMAX >= 4) {
+        const float t7 = 7.f * z2;
+        p[15] = x * y * (x2 - y2);
+        p[16] = y * z * (3.f * x2 - y2);
+        p[17] = x * y * (t7 - 1.f);
+        p[18] = y * z * (t7 - 3.f);
+        p[19] = (35.f * z2 - 30.f) * z2 + 3.f;
+        p[20] = x * z * (t7 - 3.f);
+        p[21] = (x2 - y2) * (t7 - 1.f);
+        p[22] = x * z * (x2 - 3.f * y2);
+        p[23] = x2 * (x2 - 3.f * y2) - y2 * (3.f * x2 - y2);
+      }
+    }
+  }
+}
+
+// Gradients of the same polynomials (as polynomials of x, y, z), one
+// vector per (l, m): (gx[k], gy[k], gz[k]) = grad p_k.
+template <int LMAX>
+__device__ __forceinline__ void real_harmonics_grad(float x, float y, float z, float* gx, float* gy, float* gz) {
+  gx[0] = 1.f; gy[0] = 0.f; gz[0] = 0.f;
+  gx[1] = 0.f; gy[1] = 1.f; gz[1] = 0.f;
+  gx[2] = 0.f; gy[2] = 0.f; gz[2] = 1.f;
+  if constexpr (LMAX >= 2) {
+    gx[3] = y;         gy[3] = x;          gz[3] = 0.f;
+    gx[4] = 0.f;       gy[4] = z;          gz[4] = y;
+    gx[5] = z;         gy[5] = 0.f;        gz[5] = x;
+    gx[6] = 2.f * x;   gy[6] = -2.f * y;   gz[6] = 0.f;
+    gx[7] = 0.f;       gy[7] = 0.f;        gz[7] = 6.f * z;
+    if constexpr (LMAX >= 3) {
+      const float x2 = x * x, y2 = y * y, z2 = z * z;
+      const float xy = x * y, yz = y * z, xz = x * z;
+      const float t5 = 5.f * z2 - 1.f, d3 = 3.f * x2 - 3.f * y2;
+      gx[8] = 6.f * xy;    gy[8] = d3;           gz[8] = 0.f;
+      gx[9] = yz;          gy[9] = xz;           gz[9] = xy;
+      gx[10] = 0.f;        gy[10] = t5;          gz[10] = 10.f * yz;
+      gx[11] = 0.f;        gy[11] = 0.f;         gz[11] = 15.f * z2 - 3.f;
+      gx[12] = t5;         gy[12] = 0.f;         gz[12] = 10.f * xz;
+      gx[13] = 2.f * xz;   gy[13] = -2.f * yz;   gz[13] = x2 - y2;
+      gx[14] = d3;         gy[14] = -6.f * xy;   gz[14] = 0.f;
+      if constexpr (LMAX >= 4) {
+        const float t7 = 7.f * z2 - 1.f, t73 = 7.f * z2 - 3.f, xyz = xy * z;
+        const float a15 = 3.f * x2 * y - y2 * y, b15 = x2 * x - 3.f * x * y2;
+        gx[15] = a15;                 gy[15] = b15;                 gz[15] = 0.f;
+        gx[16] = 6.f * xyz;           gy[16] = d3 * z;              gz[16] = a15;
+        gx[17] = y * t7;              gy[17] = x * t7;              gz[17] = 14.f * xyz;
+        gx[18] = 0.f;                 gy[18] = t73 * z;             gz[18] = (21.f * z2 - 3.f) * y;
+        gx[19] = 0.f;                 gy[19] = 0.f;                 gz[19] = (140.f * z2 - 60.f) * z;
+        gx[20] = t73 * z;             gy[20] = 0.f;                 gz[20] = (21.f * z2 - 3.f) * x;
+        gx[21] = 2.f * x * t7;        gy[21] = -2.f * y * t7;       gz[21] = 14.f * z * (x2 - y2);
+        gx[22] = d3 * z;              gy[22] = -6.f * xyz;          gz[22] = b15;
+        gx[23] = 4.f * x2 * x - 12.f * x * y2;  gy[23] = 4.f * y2 * y - 12.f * x2 * y;  gz[23] = 0.f;
+      }
+    }
+  }
+}
+
 }  // namespace tnep

@@ -51,43 +51,6 @@ constexpr float wlm(int k) {
 }
 constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : (k < 15 ? 3 : 4)); }
 
-// Real polynomials p_lm(x, y, z) on the unit sphere:
-// l=1: x, y, z
-// l=2: xy, yz, xz, x^2-y^2, 3z^2-1
-// l=3: y(3x^2-y^2), xyz, y(5z^2-1), z(5z^2-3), x(5z^2-1), z(x^2-y^2), x(x^2-3y^2)
-// l=4: xy(x^2-y^2), yz(3x^2-y^2), xy(7z^2-1), yz(7z^2-3), 35z^4-30z^2+3,
-//      xz(7z^2-3), (x^2-y^2)(7z^2-1), xz(x^2-3y^2), x^4-6x^2y^2+y^4
-template <int LMAX>
-__device__ __forceinline__ void real_harmonics(float x, float y, float z, float* p) {
-  p[0] = x; p[1] = y; p[2] = z;
-  if constexpr (LMAX >= 2) {
-    const float x2 = x * x, y2 = y * y, z2 = z * z;
-    p[3] = x * y; p[4] = y * z; p[5] = x * z; p[6] = x2 - y2; p[7] = 3.f * z2 - 1.f;
-    if constexpr (LMAX >= 3) {
-      const float t5 = 5.f * z2;
-      p[8] = y * (3.f * x2 - y2);
-      p[9] = x * y * z;
-      p[10] = y * (t5 - 1.f);
-      p[11] = z * (t5 - 3.f);
-      p[12] = x * (t5 - 1.f);
-      p[13] = z * (x2 - y2);
-      p[14] = x * (x2 - 3.f * y2);
-      if constexpr (LMAX >= 4) {
-        const float t7 = 7.f * z2;
-        p[15] = x * y * (x2 - y2);
-        p[16] = y * z * (3.f * x2 - y2);
-        p[17] = x * y * (t7 - 1.f);
-        p[18] = y * z * (t7 - 3.f);
-        p[19] = (35.f * z2 - 30.f) * z2 + 3.f;
-        p[20] = x * z * (t7 - 3.f);
-        p[21] = (x2 - y2) * (t7 - 1.f);
-        p[22] = x * z * (x2 - 3.f * y2);
-        p[23] = x2 * (x2 - 3.f * y2) - y2 * (3.f * x2 - y2);
-      }
-    }
-  }
-}
-
 // V += sum_lm S_lm * grad p_lm(x, y, z)  (gradient of the polynomial as written).
 // Each order l accumulates into its own partial sums so that the four
 // dependency chains run side by side.
@@ -179,7 +142,12 @@ constexpr long long kMbarTries = 1LL << 22;
 // tensor cores with BF16 operands and FP32 accumulation; 2 = the same with
 // every operand split into a high and a low BF16 part and three products
 // (hi*hi + hi*lo + lo*hi), which is accurate to about 2^-17.
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, int TCM>
+// FACT: the angular sums and the angular part of Eqs. 3-4 come from the
+// per-atom angular moments (angmom.cu) instead of a walk over the angular
+// list: A_nlm = sum_{t,k} c_nk B^t_{k,lm}, and -sum_{t,k,lm} H^t_{k,lm} Phi
+// (or Psi) with H^t_{k,lm} = sum_n G_nlm c_nk.  Exact up to rounding; used
+// for populations, whose individuals share the moments.
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, int TCM, bool FACT = false>
 __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant__ FusedArgs a) {
   constexpr bool TC = TCM != 0;
   static_assert(!TC || BLK == 128, "the tensor-core network uses M = 128 rows, one per atom");
@@ -284,8 +252,28 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     float A[NA * NLM];
 #pragma unroll
     for (int k = 0; k < NA * NLM; ++k) A[k] = 0.f;
-    NbrWalk wA(a.nbr_A, a.pos4, i, a.cap_A, 0, nA, pi);
-    for (int kk = 0; kk < nA; ++kk) {
+    if constexpr (FACT) {
+      const float* bm = a.amom + i;
+      const size_t ams = a.amom_stride;
+      for (int t = 0; t < T; ++t) {
+        const float* cblk = cA_i + t * Ly.stride_cA;
+#pragma unroll 1
+        for (int k = 0; k < BA; ++k) {
+          float ck[NA];
+#pragma unroll
+          for (int n = 0; n < NA; ++n) ck[n] = cblk[n * BA + k];
+          const float* b = bm + (size_t)((t * BA + k) * NLM) * ams;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) {
+            const float bv = b[(size_t)lm * ams];
+#pragma unroll
+            for (int n = 0; n < NA; ++n) A[n * NLM + lm] += ck[n] * bv;
+          }
+        }
+      }
+    }
+    NbrWalk wA(a.nbr_A, a.pos4, i, a.cap_A, 0, FACT ? 0 : nA, pi);
+    for (int kk = 0; kk < (FACT ? 0 : nA); ++kk) {
       const float4 pj = wA.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
       const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
@@ -502,8 +490,31 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
         for (int m = 0; m < 5; ++m) G[n * NLM + 3 + m] += e4 * gr[m];
       }
     }
-    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, 0, nA, pi);
-    for (int kk = 0; kk < nA; ++kk) {
+    if constexpr (FACT) {
+      constexpr int CC = RANK == 1 ? 3 : 9;
+      const size_t ams = a.amom_stride;
+      const float* gm = a.amom + i + (size_t)T * BA * NLM * ams;
+      for (int t = 0; t < T; ++t) {
+        const float* cblk = cA_i + t * Ly.stride_cA;
+#pragma unroll 1
+        for (int k = 0; k < BA; ++k) {
+          float ck[NA];
+#pragma unroll
+          for (int n = 0; n < NA; ++n) ck[n] = cblk[n * BA + k];
+          const float* g = gm + (size_t)((t * BA + k) * NLM) * CC * ams;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm) {
+            float h = 0.f;
+#pragma unroll
+            for (int n = 0; n < NA; ++n) h += G[n * NLM + lm] * ck[n];
+#pragma unroll
+            for (int c = 0; c < CC; ++c) acc[c] -= h * g[(size_t)(lm * CC + c) * ams];
+          }
+        }
+      }
+    }
+    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, 0, FACT ? 0 : nA, pi);
+    for (int kk = 0; kk < (FACT ? 0 : nA); ++kk) {
       const float4 pj = wB.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
       const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
@@ -561,12 +572,13 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, int TCM>
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, int TCM, bool FACT = false>
 cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
   const int nblk = (a.n_atoms + BLK - 1) / BLK;
   if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
-  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TCM> : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TCM>;
+  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TCM, FACT>
+                      : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TCM, FACT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, BLK, smem, st>>>(a);
@@ -576,6 +588,10 @@ cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, c
 template <int NR, int NA, int BR, int BA, int LMAX, bool FB>
 cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, int tcm, size_t smem,
                            cudaStream_t st) {
+  if (a.amom && tcm == 0) {
+    if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64, 0, true>(rank, a, n_pop, smem, st);
+    return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 0, true>(rank, a, n_pop, smem, st);
+  }
   if (tcm == 1) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 1>(rank, a, n_pop, smem, st);
   if (tcm == 2) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 2>(rank, a, n_pop, smem, st);
   if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64, 0>(rank, a, n_pop, smem, st);

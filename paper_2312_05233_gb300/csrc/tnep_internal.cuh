@@ -166,8 +166,23 @@ struct FusedArgs {
   size_t per_atom_stride;    // floats between individuals
   int atom_stride;           // row stride of the SoA output
   int pop_major;             // 1: blockIdx.x = individual, blockIdx.y = atom block
+  const float* amom; int amom_stride;  // angular moments (factored population path), else null
   DevStatus* status;         // error word (bounded waits of the tensor-core path)
 };
+
+// Angular moments of the basis for population evaluation (angmom.cu): B, and
+// Phi (rank 1) or Psi (rank 2), SoA with stride amom_stride.
+struct AngMomArgs {
+  int n_atoms, n_types;
+  const float4* pos4;
+  const int* sorted_struct;
+  const StructBox* boxes;
+  const int* nbr_A; const int* cnt_A; int cap_A;
+  float rc_A;
+  float* amom; int amom_stride;
+};
+size_t angular_moment_slots(int variant, int rank, int n_types);
+cudaError_t launch_angular_moments(int variant, int rank, const AngMomArgs& a, cudaStream_t st);
 
 // Kernel variant keys (must match the compiled instantiations).
 enum Variant { kVarStd = 0, kVarSmall = 1, kVarCount = 2 };

@@ -28,7 +28,8 @@ STATUS_NAMES = {
 TNEP_SPECTRUM_IR, TNEP_SPECTRUM_RAMAN_ISO, TNEP_SPECTRUM_RAMAN_ANISO = 0, 1, 2
 (TNEP_OPT_FRAMES_PER_BATCH, TNEP_OPT_MAX_NEIGHBORS, TNEP_OPT_BLOCK_ATOMS, TNEP_OPT_LAST_KERNEL_MS,
  TNEP_OPT_CELL_DIV, TNEP_OPT_LAST_KERNEL_LAUNCHES, TNEP_OPT_LAST_NBR_MS,
- TNEP_OPT_KERNEL_LAUNCHES_TOTAL, TNEP_OPT_SKIN, TNEP_OPT_LAST_SKIN_USED) = range(10)
+ TNEP_OPT_KERNEL_LAUNCHES_TOTAL, TNEP_OPT_SKIN, TNEP_OPT_LAST_SKIN_USED,
+ TNEP_OPT_POPULATION_FORM) = range(11)
 
 # Every symbol include/tnep.h declares (tests check the library exports them).
 EXPORTED = [
@@ -501,9 +502,10 @@ class Population:
         return rmse, out
 
     def info(self):
-        v = np.zeros(8)
+        v = np.zeros(13)
         _check(_lib.tnep_population_info(self.handle, v.ctypes.data))
-        return dict(block=int(v[0]), pop_major=int(v[1]), tune_ms=v[2:6].tolist(), last_ms=v[6], atoms=int(v[7]))
+        return dict(block=int(v[0]), pop_major=int(v[1]), factored=int(v[2]), tune_ms=v[3:11].tolist(),
+                    last_ms=v[11], atoms=int(v[12]))
 
     def close(self):
         if self.handle:

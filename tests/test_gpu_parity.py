@@ -414,10 +414,11 @@ def test_population_graph_replay_and_shapes(tn):
     target = rng.standard_normal((bt.n_structs, 9))
     params = [np.stack([synth.model_params(hp, rng) for _ in range(P)]) for _ in range(2)]
     ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0][0], sc)], 2, RC)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_POPULATION_FORM, 1)  # per-pair walk: same arithmetic as the batch path
     pop = tn.tnep_population_create(ctx, 0, params[0], bt.offsets, bt.pos, bt.box, bt.types, target)
     info = pop.info()
-    assert info["block"] in (64, 128) and info["atoms"] == len(bt.types)
-    assert all(t > 0 for t in info["tune_ms"])
+    assert info["block"] in (64, 128) and info["atoms"] == len(bt.types) and info["factored"] == 0
+    assert all(t > 0 for t in info["tune_ms"][:4]) and all(t == -1 for t in info["tune_ms"][4:])
     for prm in params:  # two generations with different parameters
         rmse, pred = pop.eval(prm, want_out=True)
         r1, p1 = tn.tnep_eval_population(ctx, 0, prm, bt.offsets, bt.pos, bt.box, bt.types, target, want_out=True)
@@ -431,6 +432,54 @@ def test_population_graph_replay_and_shapes(tn):
     c1.close()
     pop.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("rank,small,n_types", [(1, False, 2), (2, False, 2), (2, True, 3), (1, True, 3)])
+def test_population_factored_form(tn, rank, small, n_types):
+    """The factored form (angular sums and angular partial-force contractions
+    from per-atom moments of the basis, shared by the individuals) against the
+    FP64 oracle for every individual and structure, and against the walk."""
+    rng = np.random.default_rng(50 + rank + 3 * small)
+    if n_types == 2:
+        structs = synth.population_structures(n_clusters=6, n_boxes=1, seed_k=7)
+    else:
+        structs = []
+        for n in (20, 33, 47):
+            p, t, b = synth.anion(n, rng)
+            structs.append(synth.Structure(p.astype(np.float32), (t % 3).astype(np.int32), b.astype(np.float32)))
+        base, types, box = synth.bzo_supercell(3)
+        structs.append(synth.Structure((base + 0.05 * rng.standard_normal(base.shape)).astype(np.float32),
+                                       types.astype(np.int32), box.astype(np.float32)))
+    bt = synth.concat_structures(structs)
+    if small:
+        hp = synth.HyperParams(n_types=n_types, rank=rank, n_max_R=3, n_max_A=2, basis_R=6, basis_A=5, l_max=3,
+                               use_4body=1, n_hidden=17)
+    else:
+        hp = synth.HyperParams(n_types=n_types, rank=rank)
+    sc = synth.default_q_scaler(hp)
+    C = 3 if rank == 1 else 9
+    P = 3
+    params = np.stack([synth.model_params(hp, rng) for _ in range(P)])
+    target = rng.standard_normal((bt.n_structs, C))
+    preds = {}
+    for form in (1, 2):
+        ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc)], n_types, RC)
+        tn.tnep_set_option(ctx, tn.TNEP_OPT_POPULATION_FORM, form)
+        pop = tn.tnep_population_create(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target)
+        assert pop.info()["factored"] == (1 if form == 2 else 0)
+        rmse, preds[form] = pop.eval(params, want_out=True)
+        np.testing.assert_allclose(rmse, np.sqrt(np.mean((preds[form] - target[None]) ** 2, axis=(1, 2))),
+                                   rtol=1e-12)
+        pop.close()
+        ctx.close()
+    for p_ in range(P):
+        m = oracle.OracleModel.from_flat(hp, params[p_], sc, *RC)
+        for s_ in range(bt.n_structs):
+            a0, a1 = bt.offsets[s_], bt.offsets[s_ + 1]
+            r = oracle.evaluate(m, bt.pos[a0:a1], bt.box[s_], bt.types[a0:a1])
+            tol = max(REL * np.linalg.norm(r.tensor), COND * np.abs(r.per_atom).sum())
+            for form in (1, 2):
+                assert np.linalg.norm(preds[form][p_, s_] - r.tensor) <= tol, (form, p_, s_)
 
 
 # ------------------------------------------------- tensor-core network
