@@ -412,7 +412,8 @@ enum {
   TNEP_OPT_MAX_NEIGHBORS = 1,       /* hard cap on neighbours per atom (default 1024); lists grow up to it */
   TNEP_OPT_BLOCK_ATOMS = 2,         /* atoms per CTA of the fused kernel: 64 or 128 (default 128) */
   TNEP_OPT_LAST_KERNEL_MS = 3,      /* read-only: device time of the tensor kernels (radial moments + fused) of the last call (ms) */
-  TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2} (default 1) */
+  TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2, 3}; stencil cells
+                                       farther than the cutoff are skipped (default 1) */
   TNEP_OPT_LAST_KERNEL_LAUNCHES = 5,/* read-only: fused-kernel launches in the last call */
   TNEP_OPT_LAST_NBR_MS = 6,         /* read-only: device time of the cell/neighbour pipeline in the last call (ms) */
   TNEP_OPT_KERNEL_LAUNCHES_TOTAL = 7,/* read-only: kernels launched by this library in this process */

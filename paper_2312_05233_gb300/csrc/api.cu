@@ -149,7 +149,7 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       c->block_atoms = (int)value;
       return TNEP_OK;
     case TNEP_OPT_CELL_DIV:
-      if (value != 1 && value != 2) return fail(TNEP_ERR_INVALID, "cell subdivision must be 1 or 2");
+      if (value != 1 && value != 2 && value != 3) return fail(TNEP_ERR_INVALID, "cell subdivision must be 1, 2 or 3");
       c->cell_div = (int)value;
       return TNEP_OK;
     case TNEP_OPT_SKIN:

@@ -231,11 +231,13 @@ __global__ void k_cell_sort(NbrArgs a, int* sorted_cell) {
 }
 
 // Stencil cells along one axis with their image shift (in units of the box
-// edge, as the float32 product L * k).  Periodic axes with at least 2k+1
-// cells wrap and carry the shift that the minimum-image rule would pick for
-// any pair within the cutoff; shorter periodic axes list every cell once and
-// leave the shift to rint (flagged by the return value < 0).
-__device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* cell, float* sh) {
+// edge, as the float32 product L * k) and their distance in whole cells,
+// max(|offset| - 1, 0), from the centre cell (0 where it is not known).
+// Periodic axes with at least 2k+1 cells wrap and carry the shift that the
+// minimum-image rule would pick for any pair within the cutoff; shorter
+// periodic axes list every cell once and leave the shift to rint (flagged by
+// the return value < 0).
+__device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* cell, float* sh, int* unit) {
   int n = 0;
   if (L > 0.0f) {
     if (nc >= 2 * k + 1) {
@@ -244,18 +246,23 @@ __device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* 
         float s = 0.0f;
         if (cc < 0) { cc += nc; s = L; }
         else if (cc >= nc) { cc -= nc; s = -L; }
-        cell[n] = cc; sh[n] = s; ++n;
+        cell[n] = cc; sh[n] = s; unit[n] = max(abs(o) - 1, 0); ++n;
       }
     } else {
-      for (int o = 0; o < nc; ++o) { cell[n] = o; sh[n] = 0.0f; ++n; }
+      for (int o = 0; o < nc; ++o) { cell[n] = o; sh[n] = 0.0f; unit[n] = 0; ++n; }
       return -n;
     }
   } else {
     const int lo = max(0, c - k), hi = min(nc - 1, c + k);
-    for (int o = lo; o <= hi; ++o) { cell[n] = o; sh[n] = 0.0f; ++n; }
+    for (int o = lo; o <= hi; ++o) { cell[n] = o; sh[n] = 0.0f; unit[n] = max(abs(o - c) - 1, 0); ++n; }
   }
   return n;
 }
+
+// Lower bound on the distance between points of two cells `u` whole cells
+// apart along an axis of edge e, less a margin for positions binned across
+// a face by rounding.
+__device__ __forceinline__ float cell_gap(int u, float e) { return fmaxf((float)u * e - 1e-3f, 0.0f); }
 
 // Minimum-image difference with every operation rounded separately.
 __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
@@ -283,13 +290,14 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   const StructGrid G = a.grids[s];
   const int lc = sorted_cell[i] - G.cell_offset;
   const int cx = lc % G.nc[0], cy = (lc / G.nc[0]) % G.nc[1], cz = lc / (G.nc[0] * G.nc[1]);
-  int lx[5], ly[5], lz[5];
   const int k = a.cell_div;
-  int xc[5], yc[5], zc[5];
-  float xs[5], ys[5], zs[5];
-  int nx = axis_stencil(cx, G.nc[0], G.L[0], k, xc, xs);
-  int ny = axis_stencil(cy, G.nc[1], G.L[1], k, yc, ys);
-  int nz = axis_stencil(cz, G.nc[2], G.L[2], k, zc, zs);
+  int xc[7], yc[7], zc[7], xu[7], yu[7], zu[7];
+  float xs[7], ys[7], zs[7];
+  int nx = axis_stencil(cx, G.nc[0], G.L[0], k, xc, xs, xu);
+  int ny = axis_stencil(cy, G.nc[1], G.L[1], k, yc, ys, yu);
+  int nz = axis_stencil(cz, G.nc[2], G.L[2], k, zc, zs, zu);
+  // stencil cells farther than the cutoff from the centre cell are skipped
+  const float ex = 1.0f / G.cinv[0], ey = 1.0f / G.cinv[1], ez = 1.0f / G.cinv[2];
   // The shift of a stencil cell equals L * rint((p_j - p_i) / L) for every pair
   // the cutoff can accept when all coordinates lie in [0, L); otherwise (or
   // when an axis has too few cells to carry shifts) use rint per pair.  Both
@@ -303,14 +311,25 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
   int cR = 0, cA = 0, c1 = 0;
   for (int iz = 0; iz < nz; ++iz) {
+    const float gz = cell_gap(zu[iz], ez);
+    if (gz * gz >= rc2R) continue;
     for (int iy = 0; iy < ny; ++iy) {
+      const float gy = cell_gap(yu[iy], ey);
+      const float gyz = gy * gy + gz * gz;
+      if (gyz >= rc2R) continue;
       const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
       const float sy = ys[iy], sz = zs[iz];
       int ix = 0;
       while (ix < nx) {
-        // merge x-cells that are contiguous and share a shift into one range
+        const float gx = cell_gap(xu[ix], ex);
+        if (gx * gx + gyz >= rc2R) { ++ix; continue; }
+        // merge x-cells that are contiguous, within reach and share a shift into one range
         int ie = ix + 1;
-        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) ++ie;
+        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) {
+          const float ge = cell_gap(xu[ie], ex);
+          if (ge * ge + gyz >= rc2R) break;
+          ++ie;
+        }
         const float sx = xs[ix];
         const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
         ix = ie;

@@ -60,7 +60,7 @@ def check_frames(got, ref, per_atom_ref=None):
 
 
 # ----------------------------------------------------------- neighbour lists
-@pytest.mark.parametrize("cell_div", [1, 2])
+@pytest.mark.parametrize("cell_div", [1, 2, 3])
 def test_neighbors_bitexact(tn, cell_div):
     frames, types, box = synth.water_small(3)
     structs = [synth.Structure(frames[f], types, box) for f in range(3)]
