@@ -18,7 +18,7 @@ namespace tnep {
 namespace {
 
 template <bool HV, bool HW>
-__global__ void __launch_bounds__(128) k_radial(const __grid_constant__ RadialArgs a) {
+__global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ RadialArgs a) {
   constexpr int B = kMomBasis;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_atoms) return;
