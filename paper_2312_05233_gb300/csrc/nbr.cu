@@ -278,6 +278,38 @@ __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL
 // kernel walks one type segment at a time.  (Staging the scratch in shared
 // memory instead was measured slower: it limits the candidate scan to 12
 // warps per SM.)
+// Tests candidates jb..je-1 (at most 32) against atom i with the float32 pair
+// rule of the header, setting bit j - jb of mR / mA for r^2 < rc2R / rc2A.
+// MODE 0: no image shift; 1: a per-cell shift (s_x, s_y, s_z); 2: rint per
+// pair.  (For a zero shift modes 0 and 1 agree bit for bit.)
+template <int MODE>
+__device__ __forceinline__ void test_candidates(const float4* __restrict__ pos4, int jb, int je, float4 pi,
+                                                float sx, float sy, float sz, const StructGrid& G, float rc2R,
+                                                float rc2A, unsigned& mR, unsigned& mA) {
+  unsigned bit = 1u;
+#pragma unroll 4
+  for (int j = jb; j < je; ++j, bit <<= 1) {
+    const float4 pj = __ldg(&pos4[j]);
+    float dx, dy, dz;
+    if constexpr (MODE == 0) {
+      dx = __fsub_rn(pj.x, pi.x);
+      dy = __fsub_rn(pj.y, pi.y);
+      dz = __fsub_rn(pj.z, pi.z);
+    } else if constexpr (MODE == 1) {
+      dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
+      dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
+      dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
+    } else {
+      dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
+      dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
+      dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
+    }
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    mR |= (r2 < rc2R) ? bit : 0u;
+    mA |= (r2 < rc2A) ? bit : 0u;
+  }
+}
+
 // TWO: two atom types, radial entries written straight into their final
 // places (type 0 from entry 0 up, type 1 from entry cap_R - 1 down), with no
 // scratch list and no sort.
@@ -339,27 +371,15 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
         for (int jb = j0; jb < j1; jb += 32) {
           const int je = min(jb + 32, j1);
           unsigned mR = 0u, mA = 0u;
-#pragma unroll 4
-          for (int j = jb; j < je; ++j) {
-            const float4 pj = __ldg(&a.pos4[j]);
-            float dx, dy, dz;
-            if (noshift) {
-              dx = __fsub_rn(pj.x, pi.x);
-              dy = __fsub_rn(pj.y, pi.y);
-              dz = __fsub_rn(pj.z, pi.z);
-            } else if (!use_rint) {
-              dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
-              dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
-              dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
-            } else {
-              dx = mi_diff(pj.x, pi.x, G.L[0], G.invL[0]);
-              dy = mi_diff(pj.y, pi.y, G.L[1], G.invL[1]);
-              dz = mi_diff(pj.z, pi.z, G.L[2], G.invL[2]);
-            }
-            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            const unsigned bit = (j != i) ? (1u << (j - jb)) : 0u;
-            mR |= (r2 < rc2R) ? bit : 0u;
-            mA |= (r2 < rc2A) ? bit : 0u;
+          if (noshift)
+            test_candidates<0>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA);
+          else if (!use_rint)
+            test_candidates<1>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA);
+          else
+            test_candidates<2>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA);
+          if (i >= jb && i < je) {  // an atom is not its own neighbour
+            mR &= ~(1u << (i - jb));
+            mA &= ~(1u << (i - jb));
           }
           while (mR) {
             const int j = jb + __ffs(mR) - 1;
