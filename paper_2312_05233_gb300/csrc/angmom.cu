@@ -14,9 +14,9 @@
 // H^t_{k,lm} = sum_n (dU/dA_nlm) c^{t_i t}_{nk} the angular part of Eq. 3 is
 // -sum H . Phi and that of Eq. 4 is -sum H . Psi.
 //
-// Storage: SoA, slot-major with stride amom_stride (one float per atom):
-//   B slot      (t * BA + k) * NLM + lm
-//   Phi / Psi   T * BA * NLM + ((t * BA + k) * NLM + lm) * C + c
+// Storage (see AngMomArgs; NLMP = NLM and GBP = NLM * C, each padded to 4):
+//   B slot      (t * BA + k) * NLMP + lm
+//   Phi / Psi   T * BA * NLMP + (t * BA + k) * GBP + lm * C + c
 // One thread per atom walks its angular list once per (t, k, lm block),
 // keeping that block's sums in registers.
 
@@ -38,10 +38,9 @@ __global__ void __launch_bounds__(128) k_angular_moments(const __grid_constant__
   const StructBox bx = a.boxes[a.sorted_struct[i]];
   const float rcinv = 1.f / a.rc_A;
   const int nA = min(a.cnt_A[i], a.cap_A);
-  const size_t ms = a.amom_stride;
-  float* out = a.amom + i;
+  constexpr int NLMP = pad4(NLM), GBP = pad4(NLM * C);
   const int T = a.n_types;
-  const size_t gbase = (size_t)T * BA * NLM;
+  const int gbase = T * BA * NLMP;
   for (int t = 0; t < T; ++t) {
     for (int k = 0; k < BA; ++k) {
 #pragma unroll
@@ -89,12 +88,13 @@ __global__ void __launch_bounds__(128) k_angular_moments(const __grid_constant__
             }
           }
         }
-        const size_t b0 = (size_t)(t * BA + k) * NLM + l0;
+        const int b0 = (t * BA + k) * NLMP + l0;
+        const int g0 = gbase + (t * BA + k) * GBP + l0 * C;
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
-          out[(b0 + u) * ms] = Bs[u];
+          a.amom[amom_index(i, b0 + u, a.amom_slots)] = Bs[u];
 #pragma unroll
-          for (int c = 0; c < C; ++c) out[(gbase + (b0 + u) * C + c) * ms] = G[u * C + c];
+          for (int c = 0; c < C; ++c) a.amom[amom_index(i, g0 + u * C + c, a.amom_slots)] = G[u * C + c];
         }
       }
     }
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) k_angular_moments(const __grid_constant__
 size_t angular_moment_slots(int variant, int rank, int n_types) {
   const int BA = variant == kVarStd ? 9 : 6, LMAX = variant == kVarStd ? 4 : 3;
   const int NLM = LMAX * (LMAX + 2);
-  return (size_t)n_types * BA * NLM * (1 + (rank == 1 ? 3 : 9));
+  return (size_t)n_types * BA * (pad4(NLM) + pad4(NLM * (rank == 1 ? 3 : 9)));
 }
 
 cudaError_t launch_angular_moments(int variant, int rank, const AngMomArgs& a, cudaStream_t st) {

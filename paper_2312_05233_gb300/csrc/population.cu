@@ -59,7 +59,8 @@ FusedArgs pop_args(tnep_population* p) {
   f.pop_major = p->pop_major;
   if (p->fact) {
     f.amom = p->amom.p;
-    f.amom_stride = p->ws.atom_stride;
+    f.amom_slots = (int)angular_moment_slots(p->ctx->models[p->model].variant, p->ctx->models[p->model].d.rank,
+                                             p->ctx->n_types);
   }
   return f;
 }
@@ -198,7 +199,7 @@ tnep_status create_pop(tnep_population* p, const float* params0, const float* po
       am.cap_A = p->ws.cap_A;
       am.rc_A = c->rc_A;
       am.amom = p->amom.p;
-      am.amom_stride = p->ws.atom_stride;
+      am.amom_slots = (int)slots;
       TNEP_CUDA(launch_angular_moments(m.variant, m.d.rank, am, st));
       p->fact_ok = true;
     } else {

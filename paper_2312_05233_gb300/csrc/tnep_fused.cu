@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
 #pragma unroll
     for (int k = 0; k < NA * NLM; ++k) A[k] = 0.f;
     if constexpr (FACT) {
-      const float* bm = a.amom + i;
-      const size_t ams = a.amom_stride;
+      constexpr int NLMP = pad4(NLM);
+      // float4 group g (slots 4g..4g+3) of this atom at m4[g * 32]
+      const float4* m4 = reinterpret_cast<const float4*>(a.amom) + (size_t)(i >> 5) * (a.amom_slots / 4) * 32 + (i & 31);
       for (int t = 0; t < T; ++t) {
         const float* cblk = cA_i + t * Ly.stride_cA;
 #pragma unroll 1
@@ -262,12 +263,18 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
           float ck[NA];
 #pragma unroll
           for (int n = 0; n < NA; ++n) ck[n] = cblk[n * BA + k];
-          const float* b = bm + (size_t)((t * BA + k) * NLM) * ams;
+          const float4* b = m4 + (size_t)((t * BA + k) * (NLMP / 4)) * 32;
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) {
-            const float bv = b[(size_t)lm * ams];
+          for (int q = 0; q < NLMP / 4; ++q) {
+            const float4 v = b[(size_t)q * 32];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int n = 0; n < NA; ++n) A[n * NLM + lm] += ck[n] * bv;
+            for (int u = 0; u < 4; ++u) {
+              if (4 * q + u < NLM) {
+#pragma unroll
+                for (int n = 0; n < NA; ++n) A[n * NLM + 4 * q + u] += ck[n] * vv[u];
+              }
+            }
           }
         }
       }
@@ -492,8 +499,9 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     }
     if constexpr (FACT) {
       constexpr int CC = RANK == 1 ? 3 : 9;
-      const size_t ams = a.amom_stride;
-      const float* gm = a.amom + i + (size_t)T * BA * NLM * ams;
+      constexpr int NLMP = pad4(NLM), GBP = pad4(NLM * CC);
+      const float4* m4 = reinterpret_cast<const float4*>(a.amom) + (size_t)(i >> 5) * (a.amom_slots / 4) * 32 + (i & 31);
+      const int gbase4 = T * BA * NLMP / 4;
       for (int t = 0; t < T; ++t) {
         const float* cblk = cA_i + t * Ly.stride_cA;
 #pragma unroll 1
@@ -501,14 +509,30 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
           float ck[NA];
 #pragma unroll
           for (int n = 0; n < NA; ++n) ck[n] = cblk[n * BA + k];
-          const float* g = gm + (size_t)((t * BA + k) * NLM) * CC * ams;
+          const float4* g = m4 + (size_t)(gbase4 + (t * BA + k) * (GBP / 4)) * 32;
+          // four lm at a time: their 4 * CC slots are CC float4 groups
 #pragma unroll
-          for (int lm = 0; lm < NLM; ++lm) {
-            float h = 0.f;
+          for (int l0 = 0; l0 < NLM; l0 += 4) {
+            const int nv = (GBP - l0 * CC) / 4 < CC ? (GBP - l0 * CC) / 4 : CC;
+            float vals[4 * CC];
 #pragma unroll
-            for (int n = 0; n < NA; ++n) h += G[n * NLM + lm] * ck[n];
+            for (int q = 0; q < CC; ++q) {
+              if (q < nv) {
+                const float4 v = g[(size_t)(l0 * CC / 4 + q) * 32];
+                vals[4 * q] = v.x; vals[4 * q + 1] = v.y; vals[4 * q + 2] = v.z; vals[4 * q + 3] = v.w;
+              }
+            }
 #pragma unroll
-            for (int c = 0; c < CC; ++c) acc[c] -= h * g[(size_t)(lm * CC + c) * ams];
+            for (int u = 0; u < 4; ++u) {
+              const int lm = l0 + u;
+              if (lm < NLM) {
+                float h = 0.f;
+#pragma unroll
+                for (int n = 0; n < NA; ++n) h += G[n * NLM + lm] * ck[n];
+#pragma unroll
+                for (int c = 0; c < CC; ++c) acc[c] -= h * vals[u * CC + c];
+              }
+            }
           }
         }
       }

@@ -166,12 +166,16 @@ struct FusedArgs {
   size_t per_atom_stride;    // floats between individuals
   int atom_stride;           // row stride of the SoA output
   int pop_major;             // 1: blockIdx.x = individual, blockIdx.y = atom block
-  const float* amom; int amom_stride;  // angular moments (factored population path), else null
+  const float* amom; int amom_slots;   // angular moments (factored population path), else null
   DevStatus* status;         // error word (bounded waits of the tensor-core path)
 };
 
 // Angular moments of the basis for population evaluation (angmom.cu): B, and
-// Phi (rank 1) or Psi (rank 2), SoA with stride amom_stride.
+// Phi (rank 1) or Psi (rank 2).  Per (t, k) the B block holds NLM slots padded
+// to a multiple of 4 and the Phi / Psi block NLM * C slots padded likewise;
+// all B blocks come first.  Layout (warp-tiled, four slots per float4): slot
+// s of atom i at ((i / 32) * n_slots + (s & ~3)) * 32 + (i % 32) * 4 + (s & 3),
+// so a warp reads four consecutive slots of its 32 atoms as one 512-byte load.
 struct AngMomArgs {
   int n_atoms, n_types;
   const float4* pos4;
@@ -179,8 +183,12 @@ struct AngMomArgs {
   const StructBox* boxes;
   const int* nbr_A; const int* cnt_A; int cap_A;
   float rc_A;
-  float* amom; int amom_stride;
+  float* amom; int amom_slots;
 };
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline size_t amom_index(int i, int s, int n_slots) {
+  return ((size_t)(i >> 5) * n_slots + (s & ~3)) * 32 + (size_t)(i & 31) * 4 + (s & 3);
+}
 size_t angular_moment_slots(int variant, int rank, int n_types);
 cudaError_t launch_angular_moments(int variant, int rank, const AngMomArgs& a, cudaStream_t st);
 
