@@ -314,7 +314,10 @@ tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int 
                           double* acf_out, void* stream);
 
 /* ---------------------------------------------------------------- serving
- * Continuous batching of evaluation requests (one structure each).  Requests
+ * Continuous batching of evaluation requests (one structure each): the
+ * evaluation of Eqs. 3-4 for many independent structures (Sec. III.C notes
+ * that small systems leave a GPU limited by input/output; batching requests
+ * that arrive close together is the remedy).  Requests
  * are copied in by tnep_submit and admitted while `max_slots` requests are
  * not exceeded and the estimated device memory of the admitted, unfinished
  * requests stays within `mem_budget_bytes` (else TNEP_ERR_BUSY; retry later).
