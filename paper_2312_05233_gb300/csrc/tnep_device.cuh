@@ -70,7 +70,7 @@ __device__ __forceinline__ float min_image(float xj, float xi, float L, float in
 // is fetched two iterations ahead and its position one iteration ahead, so
 // the dependent index -> position gather overlaps the current pair's math.
 // Out-of-range slots re-use a valid index (loads stay in bounds).
-constexpr int kPrefetch = 8;
+constexpr int kPrefetch = 4;
 
 struct NbrWalk {
   const int* __restrict__ list;
