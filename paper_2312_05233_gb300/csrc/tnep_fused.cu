@@ -9,8 +9,9 @@
 //   4. radial part of the contraction through the moments V (rank 1) or W (rank 2)
 //   5. angular backward: partial force
 //        dU_i/dr_ij = s1 u + (V - (u.V) u) / r,
-//        s1 = sum_lm T_lm p_lm,  V = sum_lm S_lm grad p_lm,
-//        S_lm = sum_n G_nlm g_n(r),  T_lm = sum_n G_nlm g_n'(r),  G = dU/dA
+//        s1 = sum_lm T_lm p_lm = sum_n g_n'(r) P_n,  V = sum_lm S_lm grad p_lm,
+//        S_lm = sum_n G_nlm g_n(r),  T_lm = sum_n G_nlm g_n'(r),
+//        P_n = sum_lm G_nlm p_lm,  G = dU/dA
 // and contracts each angular partial force on the fly (Sec. II.B-C):
 //   rank 1 (Eq. 3):  mu_i    -= |r_ij|^2 dU_i/dr_ij
 //   rank 2 (Eq. 4):  alpha_i -= r_ij (x) dU_i/dr_ij,  plus U_i on the diagonal.
@@ -561,17 +562,25 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       }
       float p[NLM];
       real_harmonics<LMAX>(ux, uy, uz, p);
+      // S_lm = sum_n G_nlm g_n; sum_lm T_lm p_lm = sum_n g'_n P_n with
+      // P_n = sum_lm G_nlm p_lm
       float S[NLM];
-      float sr[4] = {0.f, 0.f, 0.f, 0.f};  // per-order partial sums of sum_lm T_lm p_lm
+      float P[NA];
+#pragma unroll
+      for (int n = 0; n < NA; ++n) P[n] = 0.f;
 #pragma unroll
       for (int lm = 0; lm < NLM; ++lm) {
-        float sv = 0.f, tv = 0.f;
+        float sv = 0.f;
 #pragma unroll
-        for (int n = 0; n < NA; ++n) { sv += G[n * NLM + lm] * g[n]; tv += G[n * NLM + lm] * dg[n]; }
+        for (int n = 0; n < NA; ++n) {
+          sv += G[n * NLM + lm] * g[n];
+          P[n] += G[n * NLM + lm] * p[lm];
+        }
         S[lm] = sv;
-        sr[l_of(lm) - 1] += tv * p[lm];
       }
-      const float srad = (sr[0] + sr[1]) + (sr[2] + sr[3]);
+      float srad = 0.f;
+#pragma unroll
+      for (int n = 0; n < NA; ++n) srad += dg[n] * P[n];
       float vx = 0.f, vy = 0.f, vz = 0.f;
       harmonic_grad<LMAX>(S, ux, uy, uz, vx, vy, vz);
       const float uv = ux * vx + uy * vy + uz * vz;
