@@ -46,8 +46,30 @@ __global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ Radia
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float rinv = rsqrtf(r2);
       const float r = r2 * rinv;
-      float f[B], df[B];
-      basis_fwd_bwd<B>(r, rcinv, f, df);
+      // basis: f_k = fc (T_k(x) + 1) / 2 enters F only through its sum, so
+      // F accumulates sum fc T_k (slot k) and is finished after the walk as
+      // F_k = (FT_k + FT_0) / 2 (T_0 = 1); f_k' = (fc' (T_k + 1) + fc x' T_k') / 2
+      float sn, cs;
+      __sincosf(kPi * r * rcinv, &sn, &cs);
+      const float fc = 0.5f + 0.5f * cs;
+      const float hdfc = -0.25f * kPi * rcinv * sn;
+      const float tt = r * rcinv - 1.f;
+      const float x = 2.f * tt * tt - 1.f, x2 = 2.f * x;
+      const float hdxfc = 2.f * tt * rcinv * fc;
+      float Tk[B], df[B];
+      {
+        float T0 = 1.f, T1 = x, d0 = 0.f, d1 = 1.f;
+        Tk[0] = 1.f; df[0] = 2.f * hdfc;
+        if constexpr (B > 1) { Tk[1] = x; df[1] = fmaf(hdxfc, 1.f, hdfc * (x + 1.f)); }
+#pragma unroll
+        for (int k = 2; k < B; ++k) {
+          const float T2 = fmaf(x2, T1, -T0);
+          const float d2 = fmaf(2.f, T1, fmaf(x2, d1, -d0));
+          Tk[k] = T2;
+          df[k] = fmaf(hdxfc, d2, hdfc * (T2 + 1.f));
+          T0 = T1; T1 = T2; d0 = d1; d1 = d2;
+        }
+      }
       // pair factors shared by every basis index k
       float rv[3], rr[6];
       if constexpr (HV) { rv[0] = r * dx; rv[1] = r * dy; rv[2] = r * dz; }
@@ -58,7 +80,7 @@ __global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ Radia
       }
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        F[k] += f[k];
+        F[k] = fmaf(fc, Tk[k], F[k]);
         if constexpr (HV) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) V[3 * k + c] = fmaf(df[k], rv[c], V[3 * k + c]);
@@ -71,7 +93,7 @@ __global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ Radia
     }
     start += n;
 #pragma unroll
-    for (int k = 0; k < B; ++k) mom[(size_t)(t * B + k) * ms] = F[k];
+    for (int k = 0; k < B; ++k) mom[(size_t)(t * B + k) * ms] = k == 0 ? F[0] : 0.5f * (F[k] + F[0]);
     if constexpr (HV) {
 #pragma unroll
       for (int k = 0; k < 3 * B; ++k) mom[(size_t)(a.v0 + 3 * t * B + k) * ms] = V[k];
