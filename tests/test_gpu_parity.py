@@ -358,6 +358,36 @@ def test_population_matches_individual_evaluation(tn):
     ctx.close()
 
 
+def test_population_full_size_sampled(tn):
+    """The population workload the bench times (50 individuals x 600 uneven
+    structures, 256,920 atoms; launch shape and angular form autotuned),
+    checked on sampled (individual, structure) pairs against the oracle."""
+    structs = synth.population_structures()
+    bt = synth.concat_structures(structs)
+    rng = np.random.default_rng(synth.seed_for(4, 11))
+    hp = synth.HyperParams(n_types=2, rank=1)
+    sc = synth.default_q_scaler(hp)
+    P = 50
+    params = np.stack([synth.model_params(hp, rng) for _ in range(P)])
+    target = synth.tensor_targets(bt.n_structs, 3, rng)
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc)], 2, RC)
+    pop = tn.tnep_population_create(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target)
+    rmse, pred = pop.eval(params, want_out=True)
+    np.testing.assert_allclose(rmse, np.sqrt(np.mean((pred - target[None]) ** 2, axis=(1, 2))), rtol=1e-12)
+    sizes = np.diff(bt.offsets)
+    small = [s for s in range(bt.n_structs) if sizes[s] <= 120]
+    big = [s for s in range(bt.n_structs) if sizes[s] >= 1000]
+    picks = [(0, small[0]), (17, small[len(small) // 2]), (49, small[-1]), (33, big[0])]
+    for p_, s_ in picks:
+        m = oracle.OracleModel.from_flat(hp, params[p_], sc, *RC)
+        a0, a1 = bt.offsets[s_], bt.offsets[s_ + 1]
+        r = oracle.evaluate(m, bt.pos[a0:a1], bt.box[s_], bt.types[a0:a1])
+        assert np.linalg.norm(pred[p_, s_] - r.tensor) <= max(REL * np.linalg.norm(r.tensor),
+                                                              COND * np.abs(r.per_atom).sum()), (p_, s_)
+    pop.close()
+    ctx.close()
+
+
 # ------------------------------------------------------------------ spectra
 @pytest.mark.parametrize("kind,C", [(0, 3), (1, 9), (2, 9)])
 def test_spectrum_parity(tn, kind, C):
