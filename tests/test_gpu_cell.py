@@ -119,3 +119,19 @@ def test_degenerate_cell_is_rejected(tn, setup):
     with pytest.raises(tn.TnepError) as e:
         tn.tnep_eval_batch_cell(ctx, [0, 3], pos, cell, np.array([0, 1, 1], np.int32))
     assert e.value.status == 1
+
+
+def test_rotated_periodic_cell_is_covariant(tn, setup):
+    # a periodic box seen in a rotated frame: the cell rows and the positions
+    # rotate together, so mu -> R mu and alpha -> R alpha R^T
+    ctx, _ = setup
+    rng = np.random.default_rng(synth.seed_for(8, 4))
+    pos, types, box = synth.water_box(216, rng, L=18.62)
+    R = synth.random_rotation(rng)
+    H = np.diag(box)
+    a = tn.tnep_eval_batch_cell(ctx, [0, len(types)], pos.astype(np.float32), H[None].astype(np.float32), types)
+    b = tn.tnep_eval_batch_cell(ctx, [0, len(types)], (pos @ R.T).astype(np.float32),
+                                (H @ R.T)[None].astype(np.float32), types)
+    mu0, al0 = a[0][0], a[1][0].reshape(3, 3)
+    np.testing.assert_allclose(b[0][0], R @ mu0, rtol=0, atol=1e-4 * np.abs(mu0).max())
+    np.testing.assert_allclose(b[1][0].reshape(3, 3), R @ al0 @ R.T, rtol=0, atol=1e-4 * np.abs(al0).max())

@@ -330,6 +330,37 @@ def test_perovskite_full_size_symmetry_and_sample(tn):
     ctx.close()
 
 
+def test_equivariance_large_open_cluster(tn):
+    """Properties that hold at any size, on a 3,000-atom open cluster: under a
+    rotation R, mu -> R mu and alpha -> R alpha R^T; translation and a
+    permutation of the atoms change nothing; alpha is symmetric."""
+    rng = np.random.default_rng(synth.seed_for(1, 60))
+    pos, types, _ = synth.water_cluster(1000, rng)
+    pos = pos.astype(np.float32)
+    ms, _ = models_for(tn, 2)
+    ctx = tn.tnep_create(ms, 2, RC)
+    offs = [0, len(types)]
+
+    def run(p, t):
+        (mu, al), (pmu, pal) = tn.tnep_eval_batch(ctx, offs, p.astype(np.float32), None, t, per_atom=True)
+        return mu[0], al[0].reshape(3, 3), np.abs(pmu).sum(), np.abs(pal).sum()
+
+    mu0, al0, s1, s2 = run(pos, types)
+    tol1, tol2 = max(REL * np.linalg.norm(mu0), COND * s1), max(REL * np.linalg.norm(al0), COND * s2)
+    R = synth.random_rotation(rng)
+    c = pos.mean(0)
+    mu1, al1, _, _ = run((pos - c) @ R.T + c, types)
+    assert np.linalg.norm(mu1 - R @ mu0) <= 2 * tol1
+    assert np.linalg.norm(al1 - R @ al0 @ R.T) <= 2 * tol2
+    mu2, al2, _, _ = run(pos + np.array([7.25, -3.5, 11.0], np.float32), types)
+    assert np.linalg.norm(mu2 - mu0) <= 2 * tol1 and np.linalg.norm(al2 - al0) <= 2 * tol2
+    perm = rng.permutation(len(types))
+    mu3, al3, _, _ = run(pos[perm], types[perm])
+    assert np.linalg.norm(mu3 - mu0) <= 2 * tol1 and np.linalg.norm(al3 - al0) <= 2 * tol2
+    assert np.linalg.norm(al0 - al0.T) <= 2 * tol2
+    ctx.close()
+
+
 # ---------------------------------------------------------------- population
 def test_population_matches_individual_evaluation(tn):
     rng = np.random.default_rng(31)
