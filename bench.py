@@ -419,7 +419,7 @@ def main():
     ap.add_argument("--cpu-centers", type=int, default=1500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--serve-rates", default="100,1000,3000,5000")
+    ap.add_argument("--serve-rates", default="100,1000,3000,5000,20000")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-population", action="store_true")
     ap.add_argument("--mlp-precision", type=int, default=0)
