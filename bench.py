@@ -308,10 +308,9 @@ def raman_bench(tn, synth, T=100_000, M=2000, n_theta=181):
     th = np.linspace(0.0, np.pi, n_theta)
     tn.tnep_raman_porto_map(L, th, 2)
     t2 = time.perf_counter()
-    fma = 81.0 * T * (M + 1) - 81.0 * M * (M + 1) / 2
     return {"workload": f"susceptibility series T = {T} (500 ps at 5 fs), M = {M} lags, {n_theta} angles",
             "tensor_ms": (t1 - t0) * 1e3, "porto_map_ms": (t2 - t1) * 1e3,
-            "fp64_gflops": 2 * fma / (t1 - t0) / 1e9}
+            "route": "fourier" if 81.0 * T * (M + 1) > 1.0e9 else "direct"}
 
 
 def precision_report(tn, synth, device, n_frames=500, oracle_frames=1):

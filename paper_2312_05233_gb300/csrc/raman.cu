@@ -4,6 +4,13 @@
 //   prep   x [9][T] channel-major, mean removed if asked
 //   corr   C_pq(tau) = sum_t x_p(t) x_q(t + tau), all 81 ordered pairs; one
 //          thread owns one pair and four consecutive lags and walks t in order
+//          (direct sums, used while 81 T M is small), or for long series
+//   fft    the symmetrised sums S_pq(tau) through the Fourier transform: the
+//          nine channels, zero-padded to N >= T + M (a power of two, so the
+//          circular correlation equals the linear one for tau <= M), are
+//          transformed (radix-2 Stockham, float64), the real cross spectra
+//          Re(conj(X_p) X_q) of the 45 pairs p <= q are transformed back two
+//          per complex transform, and S_pq(tau) = (1/N) IDFT[...](tau)
 //   cos    L_pq(nu_k) = dt [S_pq(0) + 2 sum_tau S_pq(tau) cos(pi k tau / M)],
 //          S_pq = (C_pq + C_qp) / (2 (T - tau)); one CTA per frequency, one
 //          warp per group of pairs
@@ -13,6 +20,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "engine.h"
 
 namespace tnep {
@@ -21,6 +30,8 @@ namespace {
 
 constexpr double kCmPerInvFs = 1.0 / 2.99792458e-5;
 constexpr int kLagsPerThread = 4;
+// 81 T (M + 1) above which the correlations go through the Fourier transform
+constexpr double kFftAbove = 1.0e9;
 constexpr int kCorrThreads = 128;
 
 __global__ void __launch_bounds__(1024) k_rmean(const double* __restrict__ s, int T, int subtract_mean,
@@ -75,6 +86,79 @@ __global__ void __launch_bounds__(kCorrThreads) k_rcorr(const double* __restrict
 #pragma unroll
   for (int j = 0; j < kLagsPerThread; ++j)
     if (tau0 + j <= M) C[((size_t)(tau0 + j)) * 81 + pair] = acc[j];
+}
+
+// ---- Fourier route (float64 complex as double2) ----
+
+__global__ void k_fft_twiddles(int N, double2* __restrict__ tw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N / 2) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)N, &s, &c);  // exp(-2 pi i k / N)
+  tw[k] = make_double2(c, s);
+}
+
+// Channel c of the mean-removed series, zero-padded to N, as complex.
+__global__ void k_fft_load(const double* __restrict__ x, int T, int N, double2* __restrict__ z) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 9LL * N) return;
+  const int c = (int)(g / N), t = (int)(g % N);
+  z[g] = make_double2(t < T ? x[(size_t)c * T + t] : 0.0, 0.0);
+}
+
+// One radix-2 Stockham stage (half-size p) on `batch` transforms of length
+// N: b[2j - k] = u + w v, b[2j - k + p] = u - w v with u = a[j],
+// v = a[j + N/2], k = j mod p, w = exp(-+2 pi i k / (2p)).
+__global__ void k_fft_stage(const double2* __restrict__ a, double2* __restrict__ b, const double2* __restrict__ tw,
+                            int N, int p, int batch, int inverse) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int half = N >> 1;
+  if (g >= (long long)batch * half) return;
+  const int f = (int)(g / half), j = (int)(g % half);
+  const int k = j & (p - 1);
+  double2 w = tw[(size_t)k * (half / p)];
+  if (inverse) w.y = -w.y;
+  const double2* A = a + (size_t)f * N;
+  double2* B = b + (size_t)f * N;
+  const double2 u = A[j], v0 = A[j + half];
+  const double2 v = make_double2(v0.x * w.x - v0.y * w.y, v0.x * w.y + v0.y * w.x);
+  const int o = 2 * j - k;
+  B[o] = make_double2(u.x + v.x, u.y + v.y);
+  B[o + p] = make_double2(u.x - v.x, u.y - v.y);
+}
+
+// Cross spectra of the 45 pairs p <= q, two per complex array:
+// z_w[f] = Re(conj(X_p) X_q)[f] + i Re(conj(X_p') X_q')[f].
+__global__ void k_fft_cross(const double2* __restrict__ X, int N, double2* __restrict__ z) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 23LL * N) return;
+  const int w = (int)(g / N), f = (int)(g % N);
+  double re[2] = {0.0, 0.0};
+  for (int h = 0; h < 2; ++h) {
+    const int u = 2 * w + h;
+    if (u >= 45) break;
+    int p = 0, rem = u;
+    while (rem >= 9 - p) { rem -= 9 - p; ++p; }
+    const int q = p + rem;
+    const double2 xp = X[(size_t)p * N + f], xq = X[(size_t)q * N + f];
+    re[h] = xp.x * xq.x + xp.y * xq.y;
+  }
+  z[g] = make_double2(re[0], re[1]);
+}
+
+// C[tau][81] (both p q and q p) = S_pq(tau): the inverse transform carries
+// no 1/N, so divide by N here.
+__global__ void k_fft_store(const double2* __restrict__ z, int N, int M, double* __restrict__ C) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 45LL * (M + 1)) return;
+  const int u = (int)(g / (M + 1)), tau = (int)(g % (M + 1));
+  int p = 0, rem = u;
+  while (rem >= 9 - p) { rem -= 9 - p; ++p; }
+  const int q = p + rem;
+  const double2 v = z[(size_t)(u >> 1) * N + tau];
+  const double sv = ((u & 1) ? v.y : v.x) / (double)N;
+  C[(size_t)tau * 81 + p * 9 + q] = sv;
+  C[(size_t)tau * 81 + q * 9 + p] = sv;
 }
 
 __global__ void k_rcostab(int M, double* tab) {
@@ -191,9 +275,16 @@ tnep_status tnep_raman_tensor(const double* series, int T, double dt_fs, int max
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t nS = (size_t)T * 9, nX = (size_t)T * 9, nC = (size_t)(M + 1) * 81, nT = 2 * (size_t)M;
   const size_t nF = (size_t)(M + 1), nL = (size_t)(M + 1) * 81;
+  // direct time-origin sums while they are cheap, the Fourier route beyond
+  const bool use_fft = 81.0 * (double)T * (double)(M + 1) > kFftAbove;
+  int N = 2;
+  while (N < T + M) N <<= 1;
+  const size_t nZ = use_fft ? (size_t)2 * 23 * N + (size_t)N / 2 : 0;  // double2: two work arrays + twiddles
   double* d = nullptr;
-  TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (nS + nX + nC + nT + nF + nL + 16), st));
-  double* d_s = d;
+  TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (nS + nX + nC + nT + nF + nL + 16 + 2 * nZ), st));
+  // the FFT work area (double2) first, where the allocation's alignment holds
+  double2* zwork = reinterpret_cast<double2*>(d);
+  double* d_s = d + 2 * nZ;
   double* d_x = d_s + nS;
   double* d_c = d_x + nX;
   double* d_tab = d_c + nC;
@@ -204,11 +295,34 @@ tnep_status tnep_raman_tensor(const double* series, int T, double dt_fs, int max
   if (e == cudaSuccess) {
     k_rmean<<<9, 1024, 0, st>>>(d_s, T, subtract_mean, d_mean);
     k_rprep<<<blocks_for(9LL * T, 256), 256, 0, st>>>(d_s, T, d_mean, d_x);
-    const int tiles = (M + 1 + kCorrThreads * kLagsPerThread - 1) / (kCorrThreads * kLagsPerThread);
-    k_rcorr<<<dim3(tiles, 81), kCorrThreads, 0, st>>>(d_x, T, M, d_c);
+    if (!use_fft) {
+      const int tiles = (M + 1 + kCorrThreads * kLagsPerThread - 1) / (kCorrThreads * kLagsPerThread);
+      k_rcorr<<<dim3(tiles, 81), kCorrThreads, 0, st>>>(d_x, T, M, d_c);
+      count_launches(1);
+    } else {
+      double2* za = zwork;
+      double2* zb = za + (size_t)23 * N;
+      double2* tw = zb + (size_t)23 * N;
+      k_fft_twiddles<<<blocks_for(N / 2, 256), 256, 0, st>>>(N, tw);
+      k_fft_load<<<blocks_for(9LL * N, 256), 256, 0, st>>>(d_x, T, N, za);
+      int launches = 4;
+      auto transform = [&](int batch, int inverse) {
+        for (int p = 1; p < N; p <<= 1) {
+          k_fft_stage<<<blocks_for((long long)batch * (N / 2), 256), 256, 0, st>>>(za, zb, tw, N, p, batch, inverse);
+          std::swap(za, zb);
+          ++launches;
+        }
+      };
+      transform(9, 0);
+      k_fft_cross<<<blocks_for(23LL * N, 256), 256, 0, st>>>(za, N, zb);
+      std::swap(za, zb);
+      transform(23, 1);
+      k_fft_store<<<blocks_for(45LL * (M + 1), 256), 256, 0, st>>>(za, N, M, d_c);
+      count_launches(launches);
+    }
     k_rcostab<<<blocks_for(2LL * M, 256), 256, 0, st>>>(M, d_tab);
     k_rcos<<<M + 1, 256, 0, st>>>(d_c, d_tab, T, M, dt_fs, d_f, d_l);
-    count_launches(5);
+    count_launches(4);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(freq_cm1, d_f, sizeof(double) * nF, cudaMemcpyDefault, st);

@@ -30,7 +30,9 @@ def _close(got, ref, rel=1e-10):
 
 
 @pytest.mark.parametrize("T,M,sym,sub", [(3000, 500, True, True), (3000, 7, False, True), (777, 776, True, False),
-                                         (2, 1, False, True), (1000, 513, False, False)])
+                                         (2, 1, False, True), (1000, 513, False, False),
+                                         # long enough for the Fourier route (81 T M > 1e9)
+                                         (20000, 3001, False, True), (8193, 8192, True, False)])
 def test_tensor_matches_oracle(tn, T, M, sym, sub):
     a = _series(T, T + M, sym)
     f, L = tn.tnep_raman_tensor(a, DT, M, sub)
