@@ -139,18 +139,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(hps, params, frame, box, types, n_centers, seed=0):
-    """Times the FP64 oracle (both models) on n_centers atoms of one frame."""
+def oracle_sample(hps, params, frame, box, types, n_centers, seed=0, threads=None):
+    """Times the FP64 oracle (both models) on n_centers atoms of one frame,
+    with all host threads or the number given."""
     import torch
     import oracle
     import synth
     oms = [oracle.OracleModel.from_flat(hp, p, synth.default_q_scaler(hp), *RC) for hp, p in zip(hps, params)]
     centers = np.random.default_rng(seed).choice(len(types), size=n_centers, replace=False)
-    t0 = time.perf_counter()
-    for om in oms:
-        oracle.evaluate(om, frame, box, types, centers=centers)
-    dt = time.perf_counter() - t0
-    return dt, torch.get_num_threads()
+    old = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(threads)
+    try:
+        used = torch.get_num_threads()
+        t0 = time.perf_counter()
+        for om in oms:
+            oracle.evaluate(om, frame, box, types, centers=centers)
+        dt = time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(old)
+    return dt, used
 
 
 def serving_bench(tn, synth, device, rates, n_req):
@@ -588,9 +596,12 @@ def main():
         line["served"] = serving_bench(tn, synth, local, rates, args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, cores = oracle_sample(hps, params, frames[0], box, types, args.cpu_centers)
+        n1 = max(50, args.cpu_centers // 5)
+        dt1, _ = oracle_sample(hps, params, frames[0], box, types, n1, threads=1)
         line["cpu_baseline"] = {"value": args.cpu_centers / dt, "unit": "atom-frames/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": f"{args.cpu_centers} atoms of frame 0, both models, FP64 oracle"}
+                                "sample": f"{args.cpu_centers} atoms of frame 0, both models, FP64 oracle",
+                                "single_thread": {"value": n1 / dt1, "sample": f"{n1} atoms of frame 0"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
