@@ -64,7 +64,11 @@ def traffic_record(atoms_per_pass):
     return sum(per_atom.values()) * atoms_per_pass, per_atom
 
 
-def workload_config(n_frames):
+NETWORK = {0: "FP32 on the CUDA cores", 1: "BF16 tensor cores (tcgen05), FP32 accumulation",
+           2: "split-BF16 tensor cores (tcgen05; hi/lo operands, three products, FP32 accumulation)"}
+
+
+def workload_config(n_frames, mlp_precision=2):
     return {
         "workload": f"bulk water 13,824 H2O (41,472 atoms), 74.5 A periodic cube, {n_frames}-frame random walk; "
                     "dipole (rank 1) + polarizability (rank 2) TNEP models; IR + Raman iso/aniso spectra",
@@ -72,6 +76,7 @@ def workload_config(n_frames):
         "frames": n_frames,
         "models": "rank1 + rank2, n_max 4/4, basis 8/8, l_max 4 + 4-body, H=30, rc 6/4 A",
         "l2": "inputs larger than L2 (positions 1.0 GB resident, no flush needed)",
+        "network": NETWORK[mlp_precision],
     }
 
 
@@ -429,7 +434,8 @@ def main():
     ap.add_argument("--serve-rates", default="100,1000,3000,5000,20000")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-population", action="store_true")
-    ap.add_argument("--mlp-precision", type=int, default=0)
+    ap.add_argument("--mlp-precision", type=int, default=2,
+                    help="network products: 0 FP32 CUDA cores, 1 BF16 tensor cores, 2 split-BF16 tensor cores")
     ap.add_argument("--precision-report", action="store_true")
     ap.add_argument("--skin", type=float, default=1.0, help="Verlet skin of the extra skin-reuse measurement")
     ap.add_argument("--cell-div", type=int, default=0, help="cell subdivision of the neighbour search (0 = library default)")
@@ -565,7 +571,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "atom-frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F),
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F, args.mlp_precision),
         "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "atom-frames/s",
                 "h2d_bytes_per_step": int(F * N * 12 + F * 12 + N * 4),
                 "d2h_bytes_per_step": int(F * 12 * 8 + 3 * 2 * (M + 1) * 8), "ms_per_step": e2e_ms},

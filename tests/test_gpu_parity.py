@@ -282,9 +282,16 @@ def test_errors_and_neighbor_regrow(tn):
 
 
 # ------------------------------------------- full-size workloads, sampled atoms
-def test_bulk_water_full_size_sampled(tn):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_bulk_water_full_size_sampled(tn, mode):
+    """The bench workload (41,472 atoms) with the network on the CUDA cores
+    (mode 0) and on the tensor cores with split-BF16 operands (mode 2, the
+    bench's launch configuration), sampled per-atom against the oracle."""
     frames, types, box = synth.water_bulk(n_frames=2)
     ms, om = models_for(tn, 2)
+    if mode:
+        ms = [tn.Model.from_hyper(synth.HyperParams(n_types=2, rank=m.rank), m.params, m.q_scaler, mlp_precision=mode)
+              for m in ms]
     ctx = tn.tnep_create(ms, 2, RC)
     N = len(types)
     offs = np.array([0, N])
