@@ -308,7 +308,10 @@ enum {
  * first when subtract_mean != 0.
  *   series   [T][C] (host or device), C = 3 (IR) or 9 (Raman)
  *   freq_cm1 [M+1] frequencies in cm^-1, spec [M+1] (host or device)
- *   acf_out  NULL or [M+1] the autocorrelation itself */
+ *   acf_out  NULL or [M+1] the autocorrelation itself
+ * Once channels x T x (M+1) exceeds 1e9 (channels: IR 3, iso 1, aniso 9) the
+ * autocorrelation is taken through a float64 FFT of the zero-padded series
+ * (length a power of two >= T + M); it equals the direct sums to rounding. */
 tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int kind,
                           int max_lag, int subtract_mean, double* freq_cm1, double* spec,
                           double* acf_out, void* stream);

@@ -508,18 +508,26 @@ tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t n_series = (size_t)T * C;
   const size_t n_work = (size_t)T * 9 + 3 * (size_t)(M + 1) + 2 * (size_t)M + 8;
+  // the direct time-origin sums while cheap, the Fourier route for long series
+  const bool use_fft = (double)spectrum_channels(kind) * (double)T * (double)(M + 1) > 1.0e9;
+  int N = 2;
+  while (N < T + M) N <<= 1;
+  const size_t n_z = use_fft ? (size_t)18 * N + (size_t)N / 2 : 0;  // double2
   double* d = nullptr;
-  const size_t total = n_series + n_work + 2 * (size_t)(M + 1) + (M + 1);
+  const size_t total = 2 * n_z + n_series + n_work + 2 * (size_t)(M + 1) + (M + 1);
   TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * total, st));
-  double* d_series = d;
-  double* d_work = d + n_series;
+  double2* d_z = reinterpret_cast<double2*>(d);  // first: the allocation's alignment holds
+  double* d_series = d + 2 * n_z;
+  double* d_work = d_series + n_series;
   double* d_freq = d_work + n_work;
   double* d_spec = d_freq + (M + 1);
   double* d_acf = d_spec + (M + 1);
   tnep_status rc = TNEP_OK;
   cudaError_t e = cudaMemcpyAsync(d_series, series, sizeof(double) * n_series, cudaMemcpyDefault, st);
   if (e == cudaSuccess)
-    e = launch_spectrum(d_series, T, C, dt_fs, kind, M, subtract_mean, d_work, d_freq, d_spec, d_acf, st);
+    e = use_fft ? launch_spectrum_fft(d_series, T, C, dt_fs, kind, M, subtract_mean, d_work, d_z, N, d_freq, d_spec,
+                                      d_acf, st)
+                : launch_spectrum(d_series, T, C, dt_fs, kind, M, subtract_mean, d_work, d_freq, d_spec, d_acf, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(freq_cm1, d_freq, sizeof(double) * (M + 1), cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(spec, d_spec, sizeof(double) * (M + 1), cudaMemcpyDefault, st);
   if (e == cudaSuccess && acf_out)

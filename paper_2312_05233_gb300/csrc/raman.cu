@@ -90,41 +90,12 @@ __global__ void __launch_bounds__(kCorrThreads) k_rcorr(const double* __restrict
 
 // ---- Fourier route (float64 complex as double2) ----
 
-__global__ void k_fft_twiddles(int N, double2* __restrict__ tw) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N / 2) return;
-  double s, c;
-  sincospi(-2.0 * (double)k / (double)N, &s, &c);  // exp(-2 pi i k / N)
-  tw[k] = make_double2(c, s);
-}
-
 // Channel c of the mean-removed series, zero-padded to N, as complex.
 __global__ void k_fft_load(const double* __restrict__ x, int T, int N, double2* __restrict__ z) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= 9LL * N) return;
   const int c = (int)(g / N), t = (int)(g % N);
   z[g] = make_double2(t < T ? x[(size_t)c * T + t] : 0.0, 0.0);
-}
-
-// One radix-2 Stockham stage (half-size p) on `batch` transforms of length
-// N: b[2j - k] = u + w v, b[2j - k + p] = u - w v with u = a[j],
-// v = a[j + N/2], k = j mod p, w = exp(-+2 pi i k / (2p)).
-__global__ void k_fft_stage(const double2* __restrict__ a, double2* __restrict__ b, const double2* __restrict__ tw,
-                            int N, int p, int batch, int inverse) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int half = N >> 1;
-  if (g >= (long long)batch * half) return;
-  const int f = (int)(g / half), j = (int)(g % half);
-  const int k = j & (p - 1);
-  double2 w = tw[(size_t)k * (half / p)];
-  if (inverse) w.y = -w.y;
-  const double2* A = a + (size_t)f * N;
-  double2* B = b + (size_t)f * N;
-  const double2 u = A[j], v0 = A[j + half];
-  const double2 v = make_double2(v0.x * w.x - v0.y * w.y, v0.x * w.y + v0.y * w.x);
-  const int o = 2 * j - k;
-  B[o] = make_double2(u.x + v.x, u.y + v.y);
-  B[o + p] = make_double2(u.x - v.x, u.y - v.y);
 }
 
 // Cross spectra of the 45 pairs p <= q, two per complex array:
@@ -303,22 +274,14 @@ tnep_status tnep_raman_tensor(const double* series, int T, double dt_fs, int max
       double2* za = zwork;
       double2* zb = za + (size_t)23 * N;
       double2* tw = zb + (size_t)23 * N;
-      k_fft_twiddles<<<blocks_for(N / 2, 256), 256, 0, st>>>(N, tw);
+      launch_fft_twiddles(N, tw, st);
       k_fft_load<<<blocks_for(9LL * N, 256), 256, 0, st>>>(d_x, T, N, za);
-      int launches = 4;
-      auto transform = [&](int batch, int inverse) {
-        for (int p = 1; p < N; p <<= 1) {
-          k_fft_stage<<<blocks_for((long long)batch * (N / 2), 256), 256, 0, st>>>(za, zb, tw, N, p, batch, inverse);
-          std::swap(za, zb);
-          ++launches;
-        }
-      };
-      transform(9, 0);
+      launch_fft(&za, &zb, tw, N, 9, 0, st);
       k_fft_cross<<<blocks_for(23LL * N, 256), 256, 0, st>>>(za, N, zb);
       std::swap(za, zb);
-      transform(23, 1);
+      launch_fft(&za, &zb, tw, N, 23, 1, st);
       k_fft_store<<<blocks_for(45LL * (M + 1), 256), 256, 0, st>>>(za, N, M, d_c);
-      count_launches(launches);
+      count_launches(3);
     }
     k_rcostab<<<blocks_for(2LL * M, 256), 256, 0, st>>>(M, d_tab);
     k_rcos<<<M + 1, 256, 0, st>>>(d_c, d_tab, T, M, dt_fs, d_f, d_l);

@@ -9,6 +9,13 @@
 //          (IR times (2 pi nu_k)^2), nu_k = k / (2 M dt)
 // Every sum runs in a fixed order (strided partial sums, then a tree), so the
 // results do not depend on the launch.
+// Long series (channels x T x M above 1e9) take the Fourier route for the
+// autocorrelation: the prepared channels, zero-padded to N >= T + M (a power
+// of two), are transformed (fft.cu), the real product spectrum
+//   IR: sum_c |X_c|^2 / 3,  iso: |X|^2,  aniso: sum_ab Re(conj(B_ab) B_ba)
+// is transformed back, and C(tau) = IDFT(...)(tau) / (N (T - tau)).
+
+#include <utility>
 
 #include "tnep_internal.cuh"
 
@@ -110,6 +117,43 @@ __global__ void __launch_bounds__(256) k_costransform(const double* acf, const d
   }
 }
 
+// Channel c of the prepared signal x [T][cx], zero-padded to N, as complex.
+__global__ void k_spec_load(const double* __restrict__ x, int T, int cx, int N, double2* __restrict__ z) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)cx * N) return;
+  const int c = (int)(g / N), t = (int)(g % N);
+  z[g] = make_double2(t < T ? x[(size_t)t * cx + c] : 0.0, 0.0);
+}
+
+__global__ void k_spec_product(const double2* __restrict__ X, int N, int kind, double2* __restrict__ z) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= N) return;
+  double v = 0.0;
+  if (kind == TNEP_SPECTRUM_IR) {
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = X[(size_t)c * N + f];
+      v += a.x * a.x + a.y * a.y;
+    }
+    v /= 3.0;
+  } else if (kind == TNEP_SPECTRUM_RAMAN_ISO) {
+    const double2 a = X[f];
+    v = a.x * a.x + a.y * a.y;
+  } else {
+    for (int u = 0; u < 3; ++u)
+      for (int w = 0; w < 3; ++w) {
+        const double2 a = X[(size_t)(3 * u + w) * N + f], b = X[(size_t)(3 * w + u) * N + f];
+        v += a.x * b.x + a.y * b.y;
+      }
+  }
+  z[f] = make_double2(v, 0.0);
+}
+
+__global__ void k_spec_acf(const double2* __restrict__ z, int N, int T, int M, double* __restrict__ acf) {
+  const int tau = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tau > M) return;
+  acf[tau] = z[tau].x / (double)N / (double)(T - tau);
+}
+
 }  // namespace
 
 cudaError_t launch_spectrum(const double* series, int T, int C, double dt_fs, int kind, int M,
@@ -125,6 +169,37 @@ cudaError_t launch_spectrum(const double* series, int T, int C, double dt_fs, in
   k_costransform<<<M + 1, 256, 0, st>>>(acf, tab, M, dt_fs, kind, freq, spec);
   if (acf_out) {
     cudaError_t e = cudaMemcpyAsync(acf_out, acf, sizeof(double) * (M + 1), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_fft(const double* series, int T, int C, double dt_fs, int kind, int M,
+                                int subtract_mean, double* work, double2* zwork, int N, double* freq, double* spec,
+                                double* acf_out, cudaStream_t st) {
+  const int cx = spectrum_channels(kind);
+  double* x = work;                           // [T][9]
+  double* acf = work + (size_t)T * 9;         // [M+1]
+  double* tab = acf + (M + 1);                // [2M]
+  double2* za = zwork;
+  double2* zb = za + (size_t)9 * N;
+  double2* tw = zb + (size_t)9 * N;
+  k_prep<<<1, 256, 0, st>>>(series, T, C, kind, subtract_mean, x);
+  cudaError_t e = launch_fft_twiddles(N, tw, st);
+  if (e != cudaSuccess) return e;
+  k_spec_load<<<(unsigned)(((long long)cx * N + 255) / 256), 256, 0, st>>>(x, T, cx, N, za);
+  e = launch_fft(&za, &zb, tw, N, cx, 0, st);
+  if (e != cudaSuccess) return e;
+  k_spec_product<<<(N + 255) / 256, 256, 0, st>>>(za, N, kind, zb);
+  std::swap(za, zb);
+  e = launch_fft(&za, &zb, tw, N, 1, 1, st);
+  if (e != cudaSuccess) return e;
+  k_spec_acf<<<(M + 1 + 255) / 256, 256, 0, st>>>(za, N, T, M, acf);
+  k_costab<<<(2 * M + 255) / 256, 256, 0, st>>>(M, tab);
+  k_costransform<<<M + 1, 256, 0, st>>>(acf, tab, M, dt_fs, kind, freq, spec);
+  count_launches(6);
+  if (acf_out) {
+    e = cudaMemcpyAsync(acf_out, acf, sizeof(double) * (M + 1), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();

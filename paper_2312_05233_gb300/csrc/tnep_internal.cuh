@@ -225,10 +225,25 @@ cudaError_t launch_export_neighbors(int n_atoms, const int* sorted_orig, const i
 cudaError_t launch_rmse(int n_pop, int n_structs, int C, const double* pred, const double* target,
                         double* rmse, cudaStream_t st);
 
+// Batched float64 complex FFT (fft.cu): twiddles tw[N/2] for length N (a
+// power of two); launch_fft transforms `batch` arrays of length N held in *a
+// (forward: exp(-i ...), inverse: exp(+i ...), no 1/N), using *b as the other
+// buffer, and swaps the pointers so that *a holds the result.
+cudaError_t launch_fft_twiddles(int N, double2* tw, cudaStream_t st);
+cudaError_t launch_fft(double2** a, double2** b, const double2* tw, int N, int batch, int inverse, cudaStream_t st);
+
 // Spectrum tail.
 cudaError_t launch_spectrum(const double* series, int T, int C, double dt_fs, int kind, int M,
                             int subtract_mean, double* work /* >= T*9 + 2*(M+1) + 2*M doubles */,
                             double* freq, double* spec, double* acf_out, cudaStream_t st);
+// The same through the Fourier transform for long series: N >= T + M a power
+// of two; work >= T*9 + 2*(M+1) + 2*M doubles as above, zwork >= (2*9*N + N/2)
+// double2.
+cudaError_t launch_spectrum_fft(const double* series, int T, int C, double dt_fs, int kind, int M,
+                                int subtract_mean, double* work, double2* zwork, int N, double* freq, double* spec,
+                                double* acf_out, cudaStream_t st);
+// Channels whose correlations a spectrum kind sums (IR 3, Raman iso 1, aniso 9).
+inline int spectrum_channels(int kind) { return kind == TNEP_SPECTRUM_IR ? 3 : (kind == TNEP_SPECTRUM_RAMAN_ISO ? 1 : 9); }
 
 // SNES training loop (snes.cu).
 constexpr int kMaxSnesPop = 1024;

@@ -444,6 +444,21 @@ def test_spectrum_parity(tn, kind, C):
     assert np.array_equal(S2, S)
 
 
+@pytest.mark.parametrize("kind,C,T", [(0, 3, 400_000), (1, 9, 1_100_000), (2, 9, 150_000)])
+def test_spectrum_long_series_fourier_route(tn, kind, C, T):
+    """Series long enough (channels x T x M > 1e9) for the Fourier route of
+    the autocorrelation, against the oracle's direct time-origin sums."""
+    rng = np.random.default_rng(10 + kind)
+    t = np.arange(T)
+    series = rng.normal(size=(T, C)) + np.cos(0.003 * t)[:, None] * rng.normal(size=C) + 2.0
+    f, S, acf = tn.tnep_spectrum(series, 1.0, kind, max_lag=1000, want_acf=True)
+    Cr = oracle.acf(series, 1000, kind)
+    fr, Sr = oracle.spectrum(series, 1.0, kind, max_lag=1000)
+    np.testing.assert_allclose(acf, Cr, rtol=0, atol=1e-12 * np.abs(Cr).max())
+    np.testing.assert_allclose(f, fr, rtol=1e-13)
+    np.testing.assert_allclose(S, Sr, rtol=0, atol=1e-10 * np.abs(Sr).max())
+
+
 def test_dense_cluster_large_lists(tn):
     """~200 neighbours per atom: the neighbour lists regrow well past their
     initial capacity (128 radial, 64 angular)."""
