@@ -265,6 +265,12 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
 #pragma unroll
           for (int n = 0; n < NA; ++n) ck[n] = cblk[n * BA + k];
           const float4* b = m4 + (size_t)((t * BA + k) * (NLMP / 4)) * 32;
+          // pull the next (t, k) slice towards L1 while this one is used
+          if (t * BA + k + 1 < T * BA) {
+#pragma unroll
+            for (int q = 0; q < NLMP / 4; ++q)
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(b + (size_t)(NLMP / 4 + q) * 32));
+          }
 #pragma unroll
           for (int q = 0; q < NLMP / 4; ++q) {
             const float4 v = b[(size_t)q * 32];
@@ -511,6 +517,11 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
 #pragma unroll
           for (int n = 0; n < NA; ++n) ck[n] = cblk[n * BA + k];
           const float4* g = m4 + (size_t)(gbase4 + (t * BA + k) * (GBP / 4)) * 32;
+          if (t * BA + k + 1 < T * BA) {
+#pragma unroll
+            for (int q = 0; q < GBP / 4; ++q)
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(g + (size_t)(GBP / 4 + q) * 32));
+          }
           // four lm at a time: their 4 * CC slots are CC float4 groups
 #pragma unroll
           for (int l0 = 0; l0 < NLM; l0 += 4) {
