@@ -431,9 +431,13 @@ enum {
                                        every pass with lists built per frame.  Results agree with s = 0 to float32
                                        rounding (pair order may differ). */
   TNEP_OPT_LAST_SKIN_USED = 9,      /* read-only: 1 if the last tnep_eval used skin lists in every pass */
-  TNEP_OPT_POPULATION_FORM = 10     /* angular form of populations created afterwards: 0 = the faster of the
+  TNEP_OPT_POPULATION_FORM = 10,    /* angular form of populations created afterwards: 0 = the faster of the
                                        two by timing (default), 1 = per-pair walk, 2 = factored through the
                                        angular moments (FP32 network only; otherwise the walk) */
+  TNEP_OPT_CELL_XDIV = 11           /* k_x in {1, 2, 3, 4} (default 2), used with cell_div = 1: cells of edge
+                                       rc_R / k_x along x; for k_x > 1 each atom scans, in each (y, z) row of its
+                                       stencil, only the x-cells that meet [x_i - h, x_i + h], h^2 = rc_R^2 -
+                                       (distance from atom i to the row)^2.  Same pair sets; list order may differ. */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

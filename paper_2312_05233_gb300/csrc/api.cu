@@ -152,6 +152,11 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       if (value != 1 && value != 2 && value != 3) return fail(TNEP_ERR_INVALID, "cell subdivision must be 1, 2 or 3");
       c->cell_div = (int)value;
       return TNEP_OK;
+    case TNEP_OPT_CELL_XDIV:
+      if (value != 1 && value != 2 && value != 3 && value != 4)
+        return fail(TNEP_ERR_INVALID, "x subdivision must be 1, 2, 3 or 4");
+      c->x_div = (int)value;
+      return TNEP_OK;
     case TNEP_OPT_SKIN:
       if (!(value >= 0.0) || value > 2.0) return fail(TNEP_ERR_INVALID, "skin must be in [0, 2] Angstrom");
       c->skin = (float)value;
@@ -178,6 +183,7 @@ tnep_status tnep_get_option(const tnep_ctx* c, int option, double* value) {
     case TNEP_OPT_KERNEL_LAUNCHES_TOTAL: *value = (double)launches_total(); return TNEP_OK;
     case TNEP_OPT_SKIN: *value = c->skin; return TNEP_OK;
     case TNEP_OPT_POPULATION_FORM: *value = c->population_form; return TNEP_OK;
+    case TNEP_OPT_CELL_XDIV: *value = c->x_div; return TNEP_OK;
     case TNEP_OPT_LAST_SKIN_USED: *value = c->last_skin_used; return TNEP_OK;
     default: return fail(TNEP_ERR_INVALID, "unknown option");
   }

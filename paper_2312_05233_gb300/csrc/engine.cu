@@ -181,6 +181,7 @@ tnep_status build_lists(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, const
   a.rc_R = rc_R;
   a.rc_A = rc_A;
   a.cell_div = c->cell_div;
+  a.x_div = c->x_div;
   a.grids = w.grids.p;
   a.boxes = w.boxes.p;
   a.struct_cells = w.struct_cells.p;

@@ -149,6 +149,7 @@ struct tnep_ctx {
   int max_neighbors = 1024;
   int frames_per_batch = 0;
   int cell_div = 1;
+  int x_div = 2;
   float skin = 0.f;        // Verlet skin for trajectories (0 = lists rebuilt every frame)
   int skin_cap = 160;      // radial capacity of the skin lists
   Workspace skin_ws;       // skin lists of the current pass's first frame

@@ -62,12 +62,15 @@ __global__ void k_plan(NbrArgs a) {
   StructGrid G;
   StructBox B;
   const float edge_min = a.rc_R / (float)a.cell_div * (1.0f + 1e-5f);
+  // x_div thins the cells along x (cell_div = 1 only)
+  const float edge_min_x = a.cell_div == 1 ? edge_min / (float)a.x_div : edge_min;
   int nc[3];
   float ext[3];
   for (int d = 0; d < 3; ++d) {
+    const float em = d == 0 ? edge_min_x : edge_min;
     if (L[d] > 0.0f) {
       if (L[d] < 2.0f * a.rc_R) raise_error(a.status, TNEP_ERR_BOX_TOO_SMALL, s);
-      nc[d] = max(1, (int)floorf(L[d] / edge_min));
+      nc[d] = max(1, (int)floorf(L[d] / em));
       ext[d] = L[d];
     } else if (L[d] < 0.0f || isnan(L[d])) {
       raise_error(a.status, TNEP_ERR_INVALID, s);
@@ -75,7 +78,7 @@ __global__ void k_plan(NbrArgs a) {
     } else {
       ext[d] = n > 0 ? mx[d] - mn[d] : 0.0f;
       if (!(ext[d] < 1e30f)) { raise_error(a.status, TNEP_ERR_INVALID, s); ext[d] = 0.0f; }
-      nc[d] = max(1, min(1 << 20, (int)floorf(ext[d] / edge_min) + 1));
+      nc[d] = max(1, min(1 << 20, (int)floorf(ext[d] / em) + 1));
     }
   }
   const long long cap = 2LL * n + 8;
@@ -96,7 +99,7 @@ __global__ void k_plan(NbrArgs a) {
       G.L[d] = 0.0f;
       G.invL[d] = 0.0f;
       G.origin[d] = n > 0 ? mn[d] : 0.0f;
-      const float e = fmaxf(edge_min, ext[d] / (float)nc[d] * (1.0f + 1e-6f));
+      const float e = fmaxf(d == 0 ? edge_min_x : edge_min, ext[d] / (float)nc[d] * (1.0f + 1e-6f));
       G.cinv[d] = 1.0f / e;
     }
     B.L[d] = G.L[d];
@@ -237,7 +240,9 @@ __global__ void k_cell_sort(NbrArgs a, int* sorted_cell) {
 // minimum-image rule would pick for any pair within the cutoff; shorter
 // periodic axes list every cell once and leave the shift to rint (flagged by
 // the return value < 0).
-__device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* cell, float* sh, int* unit) {
+// `off` receives each stencil cell's offset from the centre cell before wrapping.
+__device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* cell, float* sh, int* unit,
+                                            int* off) {
   int n = 0;
   if (L > 0.0f) {
     if (nc >= 2 * k + 1) {
@@ -246,15 +251,17 @@ __device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* 
         float s = 0.0f;
         if (cc < 0) { cc += nc; s = L; }
         else if (cc >= nc) { cc -= nc; s = -L; }
-        cell[n] = cc; sh[n] = s; unit[n] = max(abs(o) - 1, 0); ++n;
+        cell[n] = cc; sh[n] = s; unit[n] = max(abs(o) - 1, 0); off[n] = o; ++n;
       }
     } else {
-      for (int o = 0; o < nc; ++o) { cell[n] = o; sh[n] = 0.0f; unit[n] = 0; ++n; }
+      for (int o = 0; o < nc; ++o) { cell[n] = o; sh[n] = 0.0f; unit[n] = 0; off[n] = o - c; ++n; }
       return -n;
     }
   } else {
     const int lo = max(0, c - k), hi = min(nc - 1, c + k);
-    for (int o = lo; o <= hi; ++o) { cell[n] = o; sh[n] = 0.0f; unit[n] = max(abs(o - c) - 1, 0); ++n; }
+    for (int o = lo; o <= hi; ++o) {
+      cell[n] = o; sh[n] = 0.0f; unit[n] = max(abs(o - c) - 1, 0); off[n] = o - c; ++n;
+    }
   }
   return n;
 }
@@ -263,6 +270,19 @@ __device__ __forceinline__ int axis_stencil(int c, int nc, float L, int k, int* 
 // apart along an axis of edge e, less a margin for positions binned across
 // a face by rounding.
 __device__ __forceinline__ float cell_gap(int u, float e) { return fmaxf((float)u * e - 1e-3f, 0.0f); }
+
+// Margin (Angstrom) for float32 rounding of cell bounds, of binning and of
+// the pair rule in the window scan below.
+constexpr float kWindowMargin = 1e-3f;
+
+// Lower bound on the distance along one axis between a point at x (relative
+// to the grid origin) in cell c and the points of cell c + o, edge e.
+__device__ __forceinline__ float point_cell_gap(float x, int c, int o, float e) {
+  float g = 0.0f;
+  if (o > 0) g = (float)(c + o) * e - x;
+  else if (o < 0) g = x - (float)(c + o + 1) * e;
+  return fmaxf(g - kWindowMargin, 0.0f);
+}
 
 // Minimum-image difference with every operation rounded separately.
 __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL) {
@@ -285,7 +305,7 @@ __device__ __forceinline__ float mi_diff(float xj, float xi, float L, float invL
 template <int MODE>
 __device__ __forceinline__ void test_candidates(const float4* __restrict__ pos4, int jb, int je, float4 pi,
                                                 float sx, float sy, float sz, const StructGrid& G, float rc2R,
-                                                float rc2A, unsigned& mR, unsigned& mA) {
+                                                float rc2A, unsigned& mR, unsigned& mA, unsigned& mT) {
   unsigned bit = 1u;
 #pragma unroll 8
   for (int j = jb; j < je; ++j, bit <<= 1) {
@@ -307,6 +327,7 @@ __device__ __forceinline__ void test_candidates(const float4* __restrict__ pos4,
     const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
     mR |= (r2 < rc2R) ? bit : 0u;
     mA |= (r2 < rc2A) ? bit : 0u;
+    mT |= (__float_as_int(pj.w) != 0) ? bit : 0u;
   }
 }
 
@@ -323,11 +344,12 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   const int lc = sorted_cell[i] - G.cell_offset;
   const int cx = lc % G.nc[0], cy = (lc / G.nc[0]) % G.nc[1], cz = lc / (G.nc[0] * G.nc[1]);
   const int k = a.cell_div;
-  int xc[7], yc[7], zc[7], xu[7], yu[7], zu[7];
-  float xs[7], ys[7], zs[7];
-  int nx = axis_stencil(cx, G.nc[0], G.L[0], k, xc, xs, xu);
-  int ny = axis_stencil(cy, G.nc[1], G.L[1], k, yc, ys, yu);
-  int nz = axis_stencil(cz, G.nc[2], G.L[2], k, zc, zs, zu);
+  const int kx = k == 1 ? a.x_div : k;  // x_div subdivides x only, and only with cell_div = 1
+  int xc[9], yc[7], zc[7], xu[9], yu[7], zu[7], xo[9], yo[7], zo[7];
+  float xs[9], ys[7], zs[7];
+  int nx = axis_stencil(cx, G.nc[0], G.L[0], kx, xc, xs, xu, xo);
+  int ny = axis_stencil(cy, G.nc[1], G.L[1], k, yc, ys, yu, yo);
+  int nz = axis_stencil(cz, G.nc[2], G.L[2], k, zc, zs, zu, zo);
   // stencil cells farther than the cutoff from the centre cell are skipped
   const float ex = 1.0f / G.cinv[0], ey = 1.0f / G.cinv[1], ez = 1.0f / G.cinv[2];
   // The shift of a stencil cell equals L * rint((p_j - p_i) / L) for every pair
@@ -342,66 +364,111 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
   int* wA = a.nbr_A + (size_t)(i >> 5) * a.cap_A * 32 + (i & 31);
   int* outR = a.nbr_R + (size_t)(i >> 5) * a.cap_R * 32 + (i & 31);
   int cR = 0, cA = 0, c1 = 0;
-  for (int iz = 0; iz < nz; ++iz) {
-    const float gz = cell_gap(zu[iz], ez);
-    if (gz * gz >= rc2R) continue;
-    for (int iy = 0; iy < ny; ++iy) {
-      const float gy = cell_gap(yu[iy], ey);
-      const float gyz = gy * gy + gz * gz;
-      if (gyz >= rc2R) continue;
-      const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
-      const float sy = ys[iy], sz = zs[iz];
-      int ix = 0;
-      while (ix < nx) {
-        const float gx = cell_gap(xu[ix], ex);
-        if (gx * gx + gyz >= rc2R) { ++ix; continue; }
-        // merge x-cells that are contiguous, within reach and share a shift into one range
-        int ie = ix + 1;
-        while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) {
-          const float ge = cell_gap(xu[ie], ex);
-          if (ge * ge + gyz >= rc2R) break;
-          ++ie;
+  // Tests candidates j0..j1-1 (one contiguous range of cells sharing a shift)
+  // and appends the accepted ones.
+  auto scan = [&](int j0, int j1, float sx, float sy, float sz, bool rint_pairs) {
+    const bool noshift = !rint_pairs && sx == 0.0f && sy == 0.0f && sz == 0.0f;
+    // Test up to 32 candidates into acceptance bit masks, then append only
+    // the accepted ones (about one candidate in seven is accepted).
+    for (int jb = j0; jb < j1; jb += 32) {
+      const int je = min(jb + 32, j1);
+      unsigned mR = 0u, mA = 0u, mT = 0u;
+      if (noshift)
+        test_candidates<0>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA, mT);
+      else if (!rint_pairs)
+        test_candidates<1>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA, mT);
+      else
+        test_candidates<2>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA, mT);
+      if (i >= jb && i < je) {  // an atom is not its own neighbour
+        mR &= ~(1u << (i - jb));
+        mA &= ~(1u << (i - jb));
+      }
+      while (mR) {
+        const int b = __ffs(mR) - 1;
+        const int j = jb + b;
+        mR &= mR - 1;
+        if constexpr (TWO) {
+          if (!((mT >> b) & 1u)) {
+            if (cR - c1 < a.cap_R) outR[(size_t)(cR - c1) * 32] = j;
+          } else {
+            if (c1 < a.cap_R) outR[(size_t)(a.cap_R - 1 - c1) * 32] = j;
+            ++c1;
+          }
+        } else {
+          if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
         }
-        const float sx = xs[ix];
-        const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
-        ix = ie;
-        const bool noshift = !use_rint && sx == 0.0f && sy == 0.0f && sz == 0.0f;
-        // Test up to 32 candidates into acceptance bit masks, then append only
-        // the accepted ones (about one candidate in seven is accepted).
-        for (int jb = j0; jb < j1; jb += 32) {
-          const int je = min(jb + 32, j1);
-          unsigned mR = 0u, mA = 0u;
-          if (noshift)
-            test_candidates<0>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA);
-          else if (!use_rint)
-            test_candidates<1>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA);
-          else
-            test_candidates<2>(a.pos4, jb, je, pi, sx, sy, sz, G, rc2R, rc2A, mR, mA);
-          if (i >= jb && i < je) {  // an atom is not its own neighbour
-            mR &= ~(1u << (i - jb));
-            mA &= ~(1u << (i - jb));
+        ++cR;
+      }
+      while (mA) {
+        const int j = jb + __ffs(mA) - 1;
+        mA &= mA - 1;
+        if (cA < a.cap_A) wA[(size_t)cA * 32] = j;
+        ++cA;
+      }
+    }
+  };
+  if (kx > 1 && k == 1 && !use_rint) {
+    // Window scan: cells are thin along x.  In each (y, z) row of the stencil
+    // only the x-cells meeting [x_i - h, x_i + h] can hold pairs, where
+    // h^2 = rc_R^2 - (distance from atom i to the row)^2; on a periodic axis
+    // the window splits at the box faces into ranges with shifts +L, 0, -L.
+    // A window longer than the row falls back to the whole row with rint.
+    const float xr = pi.x - G.origin[0], yr = pi.y - G.origin[1], zr = pi.z - G.origin[2];
+    const float rcm = a.rc_R + kWindowMargin, rcm2 = rcm * rcm;
+    const int ncx = G.nc[0];
+    for (int iz = 0; iz < nz; ++iz) {
+      const float gz = point_cell_gap(zr, cz, zo[iz], ez);
+      if (gz * gz >= rcm2) continue;
+      for (int iy = 0; iy < ny; ++iy) {
+        const float gy = point_cell_gap(yr, cy, yo[iy], ey);
+        const float h2 = rcm2 - gy * gy - gz * gz;
+        if (h2 <= 0.0f) continue;
+        const float h = sqrtf(h2) + kWindowMargin;
+        int clo = (int)floorf((xr - h) * G.cinv[0]);
+        int chi = (int)floorf((xr + h) * G.cinv[0]);
+        const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * ncx;
+        const float sy = ys[iy], sz = zs[iz];
+        if (G.L[0] > 0.0f) {
+          if (chi - clo + 1 > ncx) {
+            scan(a.cell_start[row], a.cell_start[row + ncx], 0.0f, sy, sz, true);
+            continue;
           }
-          while (mR) {
-            const int j = jb + __ffs(mR) - 1;
-            mR &= mR - 1;
-            if constexpr (TWO) {
-              if (__float_as_int(a.pos4[j].w) == 0) {
-                if (cR - c1 < a.cap_R) outR[(size_t)(cR - c1) * 32] = j;
-              } else {
-                if (c1 < a.cap_R) outR[(size_t)(a.cap_R - 1 - c1) * 32] = j;
-                ++c1;
-              }
-            } else {
-              if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
-            }
-            ++cR;
+          if (clo < 0) scan(a.cell_start[row + clo + ncx], a.cell_start[row + ncx], G.L[0], sy, sz, false);
+          const int b0 = max(clo, 0), b1 = min(chi, ncx - 1);
+          if (b0 <= b1) scan(a.cell_start[row + b0], a.cell_start[row + b1 + 1], 0.0f, sy, sz, false);
+          if (chi >= ncx) scan(a.cell_start[row], a.cell_start[row + chi - ncx + 1], -G.L[0], sy, sz, false);
+        } else {
+          clo = max(clo, 0);
+          chi = min(chi, ncx - 1);
+          if (clo <= chi) scan(a.cell_start[row + clo], a.cell_start[row + chi + 1], 0.0f, sy, sz, false);
+        }
+      }
+    }
+  } else {
+    for (int iz = 0; iz < nz; ++iz) {
+      const float gz = cell_gap(zu[iz], ez);
+      if (gz * gz >= rc2R) continue;
+      for (int iy = 0; iy < ny; ++iy) {
+        const float gy = cell_gap(yu[iy], ey);
+        const float gyz = gy * gy + gz * gz;
+        if (gyz >= rc2R) continue;
+        const int row = G.cell_offset + (zc[iz] * G.nc[1] + yc[iy]) * G.nc[0];
+        const float sy = ys[iy], sz = zs[iz];
+        int ix = 0;
+        while (ix < nx) {
+          const float gx = cell_gap(xu[ix], ex);
+          if (gx * gx + gyz >= rc2R) { ++ix; continue; }
+          // merge x-cells that are contiguous, within reach and share a shift into one range
+          int ie = ix + 1;
+          while (ie < nx && xc[ie] == xc[ie - 1] + 1 && xs[ie] == xs[ix]) {
+            const float ge = cell_gap(xu[ie], ex);
+            if (ge * ge + gyz >= rc2R) break;
+            ++ie;
           }
-          while (mA) {
-            const int j = jb + __ffs(mA) - 1;
-            mA &= mA - 1;
-            if (cA < a.cap_A) wA[(size_t)cA * 32] = j;
-            ++cA;
-          }
+          const float sx = xs[ix];
+          const int j0 = a.cell_start[row + xc[ix]], j1 = a.cell_start[row + xc[ie - 1] + 1];
+          ix = ie;
+          scan(j0, j1, sx, sy, sz, use_rint);
         }
       }
     }

@@ -61,6 +61,7 @@ struct NbrArgs {
   int n_types;              // types outside [0, n_types) raise TNEP_ERR_INVALID (and read as 0)
   float rc_R, rc_A;
   int cell_div;             // cells have edge >= rc_R / cell_div
+  int x_div;                // with cell_div = 1: cells have edge >= rc_R / x_div along x (window scan)
   // outputs / scratch
   StructGrid* grids;        // [S]
   StructBox* boxes;         // [S]

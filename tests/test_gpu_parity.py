@@ -60,8 +60,17 @@ def check_frames(got, ref, per_atom_ref=None):
 
 
 # ----------------------------------------------------------- neighbour lists
-@pytest.mark.parametrize("cell_div", [1, 2, 3])
-def test_neighbors_bitexact(tn, cell_div):
+def _random_box_structure(rng, box, extent):
+    """Uniform atoms at water density in `extent` (open axes have box 0)."""
+    ext = np.asarray(extent, dtype=np.float64)
+    n = int(0.1003 * np.prod(ext))
+    pos = (rng.random((n, 3)) * ext).astype(np.float32)
+    types = (np.arange(n) % 3 != 0).astype(np.int32)
+    return synth.Structure(pos, types, np.asarray(box, dtype=np.float32))
+
+
+@pytest.mark.parametrize("cell_div,x_div", [(1, 1), (2, 1), (3, 1), (1, 2), (1, 3), (1, 4), (2, 4)])
+def test_neighbors_bitexact(tn, cell_div, x_div):
     frames, types, box = synth.water_small(3)
     structs = [synth.Structure(frames[f], types, box) for f in range(3)]
     rng = np.random.default_rng(3)
@@ -73,10 +82,22 @@ def test_neighbors_bitexact(tn, cell_div):
     for n in (1, 7, 40):
         p, t, b = synth.water_cluster(n, rng)
         structs.append(synth.Structure(p.astype(np.float32), t, b.astype(np.float32)))
+    # x barely above 2 rc_R (too few x-cells for shifts: rint per pair), x
+    # a little longer (windows wrap at both faces), a slab open along z and a
+    # rod open along x
+    structs.append(_random_box_structure(rng, (12.1, 19.0, 19.0), (12.1, 19.0, 19.0)))
+    structs.append(_random_box_structure(rng, (15.1, 19.0, 19.0), (15.1, 19.0, 19.0)))
+    structs.append(_random_box_structure(rng, (20.0, 19.0, 0.0), (20.0, 19.0, 15.0)))
+    structs.append(_random_box_structure(rng, (0.0, 18.5, 18.5), (30.0, 18.5, 18.5)))
     bt = synth.concat_structures(structs)
     ms, _ = models_for(tn, 2, ranks=(1,))
     ctx = tn.tnep_create(ms, 2, RC)
     tn.tnep_set_option(ctx, tn.TNEP_OPT_CELL_DIV, cell_div)
+    assert tn.tnep_get_option(ctx, tn.TNEP_OPT_CELL_XDIV) == 2  # the default
+    for bad in (0, 5):
+        with pytest.raises(tn.TnepError):
+            tn.tnep_set_option(ctx, tn.TNEP_OPT_CELL_XDIV, bad)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_CELL_XDIV, x_div)
     cR, cA, lR, lA = tn.tnep_neighbors(ctx, bt.offsets, bt.pos, bt.box, cap_R=256, cap_A=128)
     for s in range(bt.n_structs):
         a0, a1 = bt.offsets[s], bt.offsets[s + 1]
