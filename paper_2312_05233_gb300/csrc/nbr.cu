@@ -112,37 +112,52 @@ __global__ void k_plan(NbrArgs a) {
 }
 
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total, one CTA of 1024.
+// Tiles of 4 consecutive elements per thread (coalesced), scanned across the
+// warps and carried into the next tile.  in and out may alias: each thread
+// reads its own elements before writing them.
 __device__ void block_exclusive_scan(const int* in, int* out, int n) {
+  constexpr int V = 4;
   __shared__ int warp_sums[32];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int lo = min(n, tid * per), hi = min(n, lo + per);
-  int local = 0;
-  for (int k = lo; k < hi; ++k) local += in[k];
-  int incl = local;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  if (lane == 31) warp_sums[w] = incl;
+  __shared__ int carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) carry = 0;
   __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    int v = lane < nw ? warp_sums[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += u;
+  for (int base = 0; base < n; base += blockDim.x * V) {
+    const int k0 = base + tid * V;
+    int v[V];
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      v[q] = k0 + q < n ? in[k0 + q] : 0;
+      local += v[q];
     }
-    if (lane < nw) warp_sums[lane] = v;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int x = lane < nw ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+      }
+      if (lane < nw) warp_sums[lane] = x;
+    }
+    __syncthreads();
+    int run = carry + incl - local + (w > 0 ? warp_sums[w - 1] : 0);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      if (k0 + q < n) out[k0 + q] = run;
+      run += v[q];
+    }
+    __syncthreads();  // carry and warp_sums are read before they change
+    if (tid == blockDim.x - 1) carry = run;
+    __syncthreads();
   }
-  __syncthreads();
-  int run = incl - local + (w > 0 ? warp_sums[w - 1] : 0);
-  for (int k = lo; k < hi; ++k) {
-    const int v = in[k];
-    out[k] = run;
-    run += v;
-  }
-  if (tid == blockDim.x - 1) out[n] = run;
+  if (tid == 0) out[n] = carry;
 }
 
 __global__ void k_scan_structs(NbrArgs a) {

@@ -30,13 +30,18 @@ __global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ Radia
   int start = 0;
   for (int t = 0; t < a.n_types; ++t) {
     const int n = a.seg_R[(size_t)t * a.seg_stride + i];
-    float F[B], V[HV ? 3 * B : 1], W[HW ? 6 * B : 1];
+    // accumulators in basis pairs (k = 2q, 2q + 1), one packed multiply-add
+    // per pair; the last index of an odd basis size is accumulated alone
+    constexpr int BP = B / 2;
+    constexpr bool ODD = (B & 1) != 0;
+    f32x2 F2[BP], V2[HV ? 3 * BP : 1], W2[HW ? 6 * BP : 1];
+    float Ft = 0.f, Vt[3] = {0.f, 0.f, 0.f}, Wt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < B; ++k) F[k] = 0.f;
+    for (int q = 0; q < BP; ++q) F2[q] = 0ull;
 #pragma unroll
-    for (int k = 0; k < (HV ? 3 * B : 1); ++k) V[k] = 0.f;
+    for (int k = 0; k < (HV ? 3 * BP : 1); ++k) V2[k] = 0ull;
 #pragma unroll
-    for (int k = 0; k < (HW ? 6 * B : 1); ++k) W[k] = 0.f;
+    for (int k = 0; k < (HW ? 6 * BP : 1); ++k) W2[k] = 0ull;
     NbrWalk w(a.nbr_R, a.pos4, i, a.cap_R, radial_segment_start(a.two_ended, t, start, n, a.cap_R), n, pi);
     for (int kk = 0; kk < n; ++kk) {
       const float4 pj = w.next(kk);
@@ -78,29 +83,76 @@ __global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ Radia
         rr[0] = ux * dx; rr[1] = ux * dy; rr[2] = ux * dz;
         rr[3] = uy * dy; rr[4] = uy * dz; rr[5] = dz * rinv * dz;
       }
+      const f32x2 fcc = pk2(fc, fc);
+      f32x2 rv2[3], rr2[6];
+      if constexpr (HV) {
 #pragma unroll
-      for (int k = 0; k < B; ++k) {
-        F[k] = fmaf(fc, Tk[k], F[k]);
+        for (int c = 0; c < 3; ++c) rv2[c] = pk2(rv[c], rv[c]);
+      }
+      if constexpr (HW) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rr2[c] = pk2(rr[c], rr[c]);
+      }
+#pragma unroll
+      for (int q = 0; q < BP; ++q) {
+        const f32x2 t2 = pk2(Tk[2 * q], Tk[2 * q + 1]);
+        F2[q] = fma2(fcc, t2, F2[q]);
+        if constexpr (HV || HW) {
+          const f32x2 d2 = pk2(df[2 * q], df[2 * q + 1]);
+          if constexpr (HV) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) V2[c * BP + q] = fma2(d2, rv2[c], V2[c * BP + q]);
+          }
+          if constexpr (HW) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) W2[c * BP + q] = fma2(d2, rr2[c], W2[c * BP + q]);
+          }
+        }
+      }
+      if constexpr (ODD) {
+        Ft = fmaf(fc, Tk[B - 1], Ft);
         if constexpr (HV) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) V[3 * k + c] = fmaf(df[k], rv[c], V[3 * k + c]);
+          for (int c = 0; c < 3; ++c) Vt[c] = fmaf(df[B - 1], rv[c], Vt[c]);
         }
         if constexpr (HW) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) W[6 * k + c] = fmaf(df[k], rr[c], W[6 * k + c]);
+          for (int c = 0; c < 6; ++c) Wt[c] = fmaf(df[B - 1], rr[c], Wt[c]);
         }
       }
     }
     start += n;
+    float F[B];
+#pragma unroll
+    for (int q = 0; q < BP; ++q) unpk2(F2[q], F[2 * q], F[2 * q + 1]);
+    if constexpr (ODD) F[B - 1] = Ft;
 #pragma unroll
     for (int k = 0; k < B; ++k) mom[(size_t)(t * B + k) * ms] = k == 0 ? F[0] : 0.5f * (F[k] + F[0]);
     if constexpr (HV) {
 #pragma unroll
-      for (int k = 0; k < 3 * B; ++k) mom[(size_t)(a.v0 + 3 * t * B + k) * ms] = V[k];
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int q = 0; q < BP; ++q) {
+          float lo, hi;
+          unpk2(V2[c * BP + q], lo, hi);
+          mom[(size_t)(a.v0 + 3 * t * B + 3 * (2 * q) + c) * ms] = lo;
+          mom[(size_t)(a.v0 + 3 * t * B + 3 * (2 * q + 1) + c) * ms] = hi;
+        }
+        if constexpr (ODD) mom[(size_t)(a.v0 + 3 * t * B + 3 * (B - 1) + c) * ms] = Vt[c];
+      }
     }
     if constexpr (HW) {
 #pragma unroll
-      for (int k = 0; k < 6 * B; ++k) mom[(size_t)(a.w0 + 6 * t * B + k) * ms] = W[k];
+      for (int c = 0; c < 6; ++c) {
+#pragma unroll
+        for (int q = 0; q < BP; ++q) {
+          float lo, hi;
+          unpk2(W2[c * BP + q], lo, hi);
+          mom[(size_t)(a.w0 + 6 * t * B + 6 * (2 * q) + c) * ms] = lo;
+          mom[(size_t)(a.w0 + 6 * t * B + 6 * (2 * q + 1) + c) * ms] = hi;
+        }
+        if constexpr (ODD) mom[(size_t)(a.w0 + 6 * t * B + 6 * (B - 1) + c) * ms] = Wt[c];
+      }
     }
   }
 }

@@ -7,6 +7,24 @@ namespace tnep {
 
 constexpr float kPi = 3.14159265358979323846f;
 
+// Packed FP32 pairs (sm_100 family): two float32 lanes in one 64-bit
+// register and fma.rn.f32x2, which rounds each lane exactly like fmaf but
+// takes one issue slot for two multiply-adds.
+using f32x2 = unsigned long long;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpk2(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Chebyshev basis f_k = (T_k(x) + 1) f_c / 2, x = 2 (r/rc - 1)^2 - 1.
 template <int B>
 __device__ __forceinline__ void basis_fwd(float r, float rcinv, float* f) {

@@ -253,6 +253,11 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     float A[NA * NLM];
 #pragma unroll
     for (int k = 0; k < NA * NLM; ++k) A[k] = 0.f;
+    // the walk accumulates A in lm pairs, one packed multiply-add per pair
+    constexpr int NP = NLM / 2;
+    f32x2 A2[NA * NP];
+#pragma unroll
+    for (int k = 0; k < NA * NP; ++k) A2[k] = 0ull;
     if constexpr (FACT) {
       constexpr int NLMP = pad4(NLM);
       // float4 group g (slots 4g..4g+3) of this atom at m4[g * 32]
@@ -309,10 +314,22 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       }
       float p[NLM];
       real_harmonics<LMAX>(dx * rinv, dy * rinv, dz * rinv, p);
+      f32x2 p2[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) p2[q] = pk2(p[2 * q], p[2 * q + 1]);
+#pragma unroll
+      for (int n = 0; n < NA; ++n) {
+        const f32x2 gg = pk2(g[n], g[n]);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) A2[n * NP + q] = fma2(gg, p2[q], A2[n * NP + q]);
+        if constexpr (NLM & 1) A[n * NLM + NLM - 1] += g[n] * p[NLM - 1];
+      }
+    }
+    if constexpr (!FACT) {
 #pragma unroll
       for (int n = 0; n < NA; ++n)
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) A[n * NLM + lm] += g[n] * p[lm];
+        for (int q = 0; q < NP; ++q) unpk2(A2[n * NP + q], A[n * NLM + 2 * q], A[n * NLM + 2 * q + 1]);
     }
     // descriptor components and stash of A for the backward pass
 #pragma unroll
@@ -427,29 +444,43 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
     if (!ok && a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
   } else {
-    float s[DP];
+    // both products in descriptor pairs with packed multiply-adds: z as the
+    // sum of its even-d and odd-d halves, e accumulated pairwise
+    f32x2 s2[DP / 2], e2[DP / 2];
 #pragma unroll
-    for (int d = 0; d < DP; ++d) { s[d] = q[d] * sc[d]; e[d] = 0.f; }
+    for (int v = 0; v < DP / 2; ++v) {
+      s2[v] = pk2(q[2 * v] * sc[2 * v], q[2 * v + 1] * sc[2 * v + 1]);
+      e2[v] = 0ull;
+    }
     for (int h = 0; h < Ly.H; ++h) {
       const float4* row = reinterpret_cast<const float4*>(W0 + h * DP);
-      float z = -b0[h];
+      f32x2 z2 = 0ull;
 #pragma unroll
       for (int v = 0; v < DP / 4; ++v) {
         const float4 w = row[v];
-        z += w.x * s[4 * v] + w.y * s[4 * v + 1] + w.z * s[4 * v + 2] + w.w * s[4 * v + 3];
+        z2 = fma2(pk2(w.x, w.y), s2[2 * v], z2);
+        z2 = fma2(pk2(w.z, w.w), s2[2 * v + 1], z2);
       }
-      const float hh = tanhf(z);
+      float zl, zh;
+      unpk2(z2, zl, zh);
+      const float hh = tanhf(zl + zh - b0[h]);
       const float wh = w1[h];
       U += wh * hh;
       const float vh = wh * (1.f - hh * hh);
+      const f32x2 vv = pk2(vh, vh);
 #pragma unroll
       for (int v = 0; v < DP / 4; ++v) {
         const float4 w = row[v];
-        e[4 * v] += vh * w.x; e[4 * v + 1] += vh * w.y; e[4 * v + 2] += vh * w.z; e[4 * v + 3] += vh * w.w;
+        e2[2 * v] = fma2(vv, pk2(w.x, w.y), e2[2 * v]);
+        e2[2 * v + 1] = fma2(vv, pk2(w.z, w.w), e2[2 * v + 1]);
       }
     }
 #pragma unroll
-    for (int d = 0; d < DP; ++d) e[d] *= sc[d];
+    for (int v = 0; v < DP / 2; ++v) {
+      unpk2(e2[v], e[2 * v], e[2 * v + 1]);
+      e[2 * v] *= sc[2 * v];
+      e[2 * v + 1] *= sc[2 * v + 1];
+    }
   }
 
   float acc[C];
@@ -504,6 +535,13 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
         for (int m = 0; m < 5; ++m) G[n * NLM + 3 + m] += e4 * gr[m];
       }
     }
+    // G in lm pairs for the packed products of the pair walk
+    constexpr int NP = NLM / 2;
+    f32x2 G2[NA * NP];
+#pragma unroll
+    for (int n = 0; n < NA; ++n)
+#pragma unroll
+      for (int q = 0; q < NP; ++q) G2[n * NP + q] = pk2(G[n * NLM + 2 * q], G[n * NLM + 2 * q + 1]);
     if constexpr (FACT) {
       constexpr int CC = RANK == 1 ? 3 : 9;
       constexpr int NLMP = pad4(NLM), GBP = pad4(NLM * CC);
@@ -574,20 +612,38 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       float p[NLM];
       real_harmonics<LMAX>(ux, uy, uz, p);
       // S_lm = sum_n G_nlm g_n; sum_lm T_lm p_lm = sum_n g'_n P_n with
-      // P_n = sum_lm G_nlm p_lm
+      // P_n = sum_lm G_nlm p_lm.  Both run over lm pairs with packed
+      // multiply-adds; P_n is summed as its even-lm and odd-lm halves.
       float S[NLM];
+      f32x2 gg[NA], P2[NA];
+#pragma unroll
+      for (int n = 0; n < NA; ++n) { gg[n] = pk2(g[n], g[n]); P2[n] = 0ull; }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const f32x2 pq = pk2(p[2 * q], p[2 * q + 1]);
+        f32x2 sv = 0ull;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+          sv = fma2(G2[n * NP + q], gg[n], sv);
+          P2[n] = fma2(G2[n * NP + q], pq, P2[n]);
+        }
+        unpk2(sv, S[2 * q], S[2 * q + 1]);
+      }
       float P[NA];
 #pragma unroll
-      for (int n = 0; n < NA; ++n) P[n] = 0.f;
-#pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) {
+      for (int n = 0; n < NA; ++n) {
+        float lo, hi;
+        unpk2(P2[n], lo, hi);
+        P[n] = lo + hi;
+      }
+      if constexpr (NLM & 1) {
         float sv = 0.f;
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
-          sv += G[n * NLM + lm] * g[n];
-          P[n] += G[n * NLM + lm] * p[lm];
+          sv += G[n * NLM + NLM - 1] * g[n];
+          P[n] += G[n * NLM + NLM - 1] * p[NLM - 1];
         }
-        S[lm] = sv;
+        S[NLM - 1] = sv;
       }
       float srad = 0.f;
 #pragma unroll
