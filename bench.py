@@ -434,6 +434,8 @@ def main():
     ap.add_argument("--serve-rates", default="100,1000,3000,5000,20000")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-population", action="store_true")
+    ap.add_argument("--no-network-variants", action="store_true",
+                    help="skip timing the step with the network in the other precisions")
     ap.add_argument("--mlp-precision", type=int, default=2,
                     help="network products: 0 FP32 CUDA cores, 1 BF16 tensor cores, 2 split-BF16 tensor cores")
     ap.add_argument("--precision-report", action="store_true")
@@ -556,6 +558,37 @@ def main():
                      "nbr_ms_per_step": tn.tnep_get_option(ctx, tn.TNEP_OPT_LAST_NBR_MS)}
         tn.tnep_set_option(ctx, tn.TNEP_OPT_SKIN, 0.0)
 
+    # the same step with the network in the other precisions (same weights)
+    variants = {}
+    if rank == 0 and not args.no_network_variants:
+        for mp in (0, 1, 2):
+            if mp == args.mlp_precision:
+                continue
+            vmodels, _, _ = make_models(tn, synth, mp)
+            vctx = tn.tnep_create(vmodels, 2, RC, device=local)
+            if args.cell_div:
+                tn.tnep_set_option(vctx, tn.TNEP_OPT_CELL_DIV, args.cell_div)
+            if args.x_div:
+                tn.tnep_set_option(vctx, tn.TNEP_OPT_CELL_XDIV, args.x_div)
+
+            def vstep():
+                tn.tnep_eval(vctx, pos_d, box_d, types_d, out=out_d, stream=sp)
+                tn.tnep_spectrum(out_d[:F * 3].view(F, 3), DT_FS, tn.TNEP_SPECTRUM_IR, M, stream=sp)
+                tn.tnep_spectrum(out_d[F * 3:].view(F, 9), DT_FS, tn.TNEP_SPECTRUM_RAMAN_ISO, M, stream=sp)
+                tn.tnep_spectrum(out_d[F * 3:].view(F, 9), DT_FS, tn.TNEP_SPECTRUM_RAMAN_ANISO, M, stream=sp)
+
+            for _ in range(2):
+                vstep()
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                vstep()
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            v_ms = ev0.elapsed_time(ev1) / args.steps
+            variants[NETWORK[mp]] = {"value": F * N / (v_ms * 1e-3), "ms_per_step": v_ms}
+            vctx.close()
+
     # neighbour statistics of the last frame for the flop model
     offs = np.array([0, N])
     cR, cA, _, _ = tn.tnep_neighbors(ctx, offs, frames[-1], box[None], cap_R=1, cap_A=1)
@@ -591,6 +624,7 @@ def main():
                      "fused_launches_per_step": fused_launches / args.steps},
         "clocks": clocks,
         "skin_reuse": skin_line,
+        "network_variants": variants or None,
     }
     if rank == 0 and args.precision_report:
         line["precision"] = precision_report(tn, synth, local)
