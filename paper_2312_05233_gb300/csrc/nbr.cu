@@ -4,7 +4,8 @@
 // r_ij = r_j - r_i taken under the minimum image (Sec. II.A).  The pipeline
 // per batch is:
 //   plan    one CTA per structure: box checks, bounding box of open axes,
-//           cell grid with edge >= rc_R / cell_div (at most 2n + 8 cells)
+//           cell grid with edge >= rc_R / cell_div (>= rc_R / x_div along x
+//           when cell_div = 1; at most 2n + 8 cells)
 //   scan    exclusive scan of cells per structure
 //   bin     cell of every atom, atomic slot inside the cell
 //   scan    exclusive scan of cell counts
@@ -12,8 +13,10 @@
 //   sort    one warp per cell orders its atoms by input index (so the whole
 //           pipeline is deterministic) and writes cell-ordered float4
 //           positions with the type in .w
-//   build   one thread per atom scans the stencil cells and writes the
-//           radial (rc_R) and angular (rc_A) lists, warp-tiled.
+//   build   one thread per atom scans the stencil cells (with x-thin cells:
+//           only the x-cells of each stencil row that its cutoff sphere
+//           reaches) and writes the radial (rc_R) and angular (rc_A) lists,
+//           warp-tiled.
 // Pair selection follows the exact float32 recipe documented in tnep.h.
 
 #include "tnep_internal.cuh"
