@@ -224,13 +224,14 @@ def pairs_cell(pos, cell, rc, centers=None):
     return I[order], J[order], R[order]
 
 
-def neighbours_fp32(pos, box, rc):
+def neighbours_fp32(pos, box, rc, atoms=None):
     """Pair sets under the exact FP32 recipe the C header specifies.
 
     d = p_j - p_i; on a periodic axis d = d - L * rint(d * (1/L)); every
     operation rounded to float32 separately (no fused multiply-add);
     r2 = (dx*dx + dy*dy) + dz*dz; pair iff r2 < rc*rc (rounded to float32).
-    Returns a list of sorted int arrays, one per atom.
+    Returns a list of sorted int arrays, one per atom (per atom of `atoms`
+    when given: each atom's set is computed on its own against all atoms).
     """
     p = np.asarray(pos, dtype=np.float32)
     b = np.asarray(box, dtype=np.float32)
@@ -239,7 +240,7 @@ def neighbours_fp32(pos, box, rc):
     rc2 = np.float32(rc32 * rc32)
     inv = np.where(b > 0, np.float32(1.0) / np.where(b > 0, b, np.float32(1.0)), np.float32(0.0)).astype(np.float32)
     out = []
-    for i in range(n):
+    for i in (range(n) if atoms is None else atoms):
         d = (p - p[i]).astype(np.float32)
         for a in range(3):
             if b[a] > 0:

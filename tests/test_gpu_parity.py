@@ -111,6 +111,25 @@ def test_neighbors_bitexact(tn, cell_div, x_div):
     ctx.close()
 
 
+def test_neighbors_bitexact_bulk_water(tn):
+    """The bench's frame size (41,472 atoms, 74.5 A box) with the default
+    x-thin cells: sampled atoms' lists against the float32 brute force."""
+    frames, types, box = synth.water_bulk(n_frames=1)
+    pos = frames[0]
+    ms, _ = models_for(tn, 2, ranks=(1,))
+    ctx = tn.tnep_create(ms, 2, RC)
+    offs = np.array([0, len(pos)], np.int32)
+    cR, cA, lR, lA = tn.tnep_neighbors(ctx, offs, pos, box[None, :], cap_R=256, cap_A=128)
+    sample = np.random.default_rng(11).choice(len(pos), size=1500, replace=False)
+    refR = oracle.neighbours_fp32(pos, box, RC[0], atoms=sample)
+    refA = oracle.neighbours_fp32(pos, box, RC[1], atoms=sample)
+    for a, rR, rA in zip(sample, refR, refA):
+        assert cR[a] == len(rR) and cA[a] == len(rA)
+        assert np.array_equal(np.sort(lR[a, :cR[a]]), rR)
+        assert np.array_equal(np.sort(lA[a, :cA[a]]), rA)
+    ctx.close()
+
+
 # ------------------------------------------------------- small water (192 atoms)
 def test_water_small_parity(tn):
     frames, types, box = synth.water_small(12)
