@@ -401,21 +401,29 @@ __global__ void __launch_bounds__(128) k_build(NbrArgs a, const int* sorted_cell
         mR &= ~(1u << (i - jb));
         mA &= ~(1u << (i - jb));
       }
-      while (mR) {
-        const int b = __ffs(mR) - 1;
-        const int j = jb + b;
-        mR &= mR - 1;
-        if constexpr (TWO) {
-          if (!((mT >> b) & 1u)) {
-            if (cR - c1 < a.cap_R) outR[(size_t)(cR - c1) * 32] = j;
-          } else {
-            if (c1 < a.cap_R) outR[(size_t)(a.cap_R - 1 - c1) * 32] = j;
-            ++c1;
-          }
-        } else {
-          if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
+      if constexpr (TWO) {
+        // type 0 from the front, then type 1 from the back: one store stream each
+        unsigned m0 = mR & ~mT, m1 = mR & mT;
+        while (m0) {
+          const int j = jb + __ffs(m0) - 1;
+          m0 &= m0 - 1;
+          if (cR - c1 < a.cap_R) outR[(size_t)(cR - c1) * 32] = j;
+          ++cR;
         }
-        ++cR;
+        while (m1) {
+          const int j = jb + __ffs(m1) - 1;
+          m1 &= m1 - 1;
+          if (c1 < a.cap_R) outR[(size_t)(a.cap_R - 1 - c1) * 32] = j;
+          ++c1;
+          ++cR;
+        }
+      } else {
+        while (mR) {
+          const int j = jb + __ffs(mR) - 1;
+          mR &= mR - 1;
+          if (cR < a.cap_R) wR[(size_t)cR * 32] = j | (__float_as_int(a.pos4[j].w) << kTypeShift);
+          ++cR;
+        }
       }
       while (mA) {
         const int j = jb + __ffs(mA) - 1;
