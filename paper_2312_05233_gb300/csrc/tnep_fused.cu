@@ -727,78 +727,6 @@ cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, i
   return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 0>(rank, a, n_pop, smem, st);
 }
 
-// Per-structure FP64 sums in two deterministic stages: CTA (s, chunk) sums a
-// fixed 2048-atom chunk of structure s (strided per-thread sums, then a
-// tree), then one thread per structure adds its chunk partials in order.
-// Chunks are aligned to the structure start, so a structure's result does
-// not depend on what else is in the batch.
-__global__ void __launch_bounds__(256) k_reduce_partial(const int* offsets, int n_chunks, const float* per_atom,
-                                                        size_t pa_pop_stride, int atom_stride, int C,
-                                                        double* partial) {
-  const int s = blockIdx.x / n_chunks, chunk = blockIdx.x % n_chunks, p = blockIdx.y;
-  const int S = gridDim.x / n_chunks;
-  const int a0 = offsets[s] + chunk * kReduceChunk;
-  const int a1 = min(offsets[s + 1], a0 + kReduceChunk);
-  const float* pa = per_atom + (size_t)p * pa_pop_stride;
-  double acc[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-  for (int g = a0 + threadIdx.x; g < a1; g += blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 9; ++c)
-      if (c < C) acc[c] += (double)pa[(size_t)c * atom_stride + g];
-  }
-  __shared__ double red[9][256];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) red[c][threadIdx.x] = acc[c];
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-#pragma unroll
-      for (int c = 0; c < 9; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < C) partial[(((size_t)p * S + s) * n_chunks + chunk) * C + threadIdx.x] = red[threadIdx.x][0];
-}
-
-__global__ void k_reduce_final(int S, int n_chunks, int C, int n_pop, const double* partial, double* out,
-                               size_t out_pop_stride) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= S * n_pop) return;
-  const int p = t / S, s = t % S;
-  const double* src = partial + ((size_t)p * S + s) * n_chunks * C;
-  for (int c = 0; c < C; ++c) {
-    double v = 0.0;
-    for (int k = 0; k < n_chunks; ++k) v += src[(size_t)k * C + c];
-    out[(size_t)p * out_pop_stride + (size_t)s * C + c] = v;
-  }
-}
-
-__global__ void k_gather(int n, const int* orig_sorted, const float* pa, int atom_stride, int C, float* out) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const int i = orig_sorted[g];
-  for (int c = 0; c < C; ++c) out[(size_t)g * C + c] = pa[(size_t)c * atom_stride + i];
-}
-
-__global__ void k_rmse(int S, int C, const double* pred, const double* target, double* rmse) {
-  const int p = blockIdx.x;
-  const double* pp = pred + (size_t)p * S * C;
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < S * C; k += blockDim.x) {
-    const double d = pp[k] - target[k];
-    acc += d * d;
-  }
-  __shared__ double red[256];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) rmse[p] = S * C > 0 ? sqrt(red[0] / (double)(S * C)) : 0.0;
-}
-
 }  // namespace
 
 static std::atomic<long long> g_launches{0};
@@ -832,35 +760,6 @@ cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, i
     case kVarSmall: return launch_variant<4, 3, 7, 6, 3, true>(rank, a, n_pop, block, tcm, smem, st);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_reduce(int n_structs, int n_pop, const int* offsets, int max_atoms, const float* per_atom,
-                          size_t per_atom_stride, int atom_stride, int C, double* partial, double* out,
-                          size_t out_pop_stride, cudaStream_t st) {
-  if (n_structs <= 0 || n_pop <= 0) return cudaSuccess;
-  count_launches(2);
-  const int n_chunks = reduce_chunks(max_atoms);
-  k_reduce_partial<<<dim3(n_structs * n_chunks, n_pop), 256, 0, st>>>(offsets, n_chunks, per_atom, per_atom_stride,
-                                                                     atom_stride, C, partial);
-  const int nt = n_structs * n_pop;
-  k_reduce_final<<<(nt + 127) / 128, 128, 0, st>>>(n_structs, n_chunks, C, n_pop, partial, out, out_pop_stride);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gather_per_atom(int n_atoms, const int* orig_sorted, const float* per_atom,
-                                   int atom_stride, int C, float* out, cudaStream_t st) {
-  if (n_atoms <= 0) return cudaSuccess;
-  count_launches(1);
-  k_gather<<<(n_atoms + 255) / 256, 256, 0, st>>>(n_atoms, orig_sorted, per_atom, atom_stride, C, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_rmse(int n_pop, int n_structs, int C, const double* pred, const double* target,
-                        double* rmse, cudaStream_t st) {
-  if (n_pop <= 0) return cudaSuccess;
-  count_launches(1);
-  k_rmse<<<n_pop, 256, 0, st>>>(n_structs, C, pred, target, rmse);
-  return cudaGetLastError();
 }
 
 }  // namespace tnep
