@@ -442,6 +442,7 @@ def main():
     ap.add_argument("--skin", type=float, default=1.0, help="Verlet skin of the extra skin-reuse measurement")
     ap.add_argument("--cell-div", type=int, default=0, help="cell subdivision of the neighbour search (0 = library default)")
     ap.add_argument("--x-div", type=int, default=0, help="x-only cell subdivision with window scan (0 = library default)")
+    ap.add_argument("--frames-per-batch", type=int, default=0, help="frames per device pass (0 = library default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -474,6 +475,8 @@ def main():
         tn.tnep_set_option(ctx, tn.TNEP_OPT_CELL_DIV, args.cell_div)
     if args.x_div:
         tn.tnep_set_option(ctx, tn.TNEP_OPT_CELL_XDIV, args.x_div)
+    if args.frames_per_batch:
+        tn.tnep_set_option(ctx, tn.TNEP_OPT_FRAMES_PER_BATCH, args.frames_per_batch)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
 

@@ -427,7 +427,11 @@ cudaStream_t pick_stream(tnep_ctx* c, void* stream) {
 }
 
 int default_frames_per_batch(int n_atoms, int n_frames) {
-  const long long target = 1 << 20;  // ~1 M atoms per pass: >= 20 waves of 304 CTAs
+  // ~2 M atoms per pass: > 50 waves of 304 CTAs of the fused kernel, and the
+  // fixed costs of a pass (small neighbour kernels, reductions, kernel tails)
+  // spread over many frames (bulk water, 2,000 frames: 418.6 ms per step at
+  // 25 frames per pass, 409.1 ms at 50, 407.7 ms at 64)
+  const long long target = 1 << 21;
   long long fb = std::max<long long>(1, target / std::max(n_atoms, 1));
   return (int)std::min<long long>(fb, std::max(n_frames, 1));
 }
