@@ -18,7 +18,7 @@ namespace tnep {
 namespace {
 
 template <bool HV, bool HW>
-__global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ RadialArgs a) {
+__global__ void __launch_bounds__(128, 3) k_radial(const __grid_constant__ RadialArgs a) {
   constexpr int B = kMomBasis;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_atoms) return;
@@ -43,6 +43,9 @@ __global__ void __launch_bounds__(128, 4) k_radial(const __grid_constant__ Radia
 #pragma unroll
     for (int k = 0; k < (HW ? 6 * BP : 1); ++k) W2[k] = 0ull;
     NbrWalk w(a.nbr_R, a.pos4, i, a.cap_R, radial_segment_start(a.two_ended, t, start, n, a.cap_R), n, pi);
+    // two pairs per iteration interleave their (serial) basis recursions;
+    // 166 registers, three CTAs per SM
+#pragma unroll 2
     for (int kk = 0; kk < n; ++kk) {
       const float4 pj = w.next(kk);
       const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
