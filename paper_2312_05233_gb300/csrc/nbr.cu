@@ -325,7 +325,7 @@ __device__ __forceinline__ void test_candidates(const float4* __restrict__ pos4,
                                                 float sx, float sy, float sz, const StructGrid& G, float rc2R,
                                                 float rc2A, unsigned& mR, unsigned& mA, unsigned& mT) {
   unsigned bit = 1u;
-#pragma unroll 8
+#pragma unroll 4
   for (int j = jb; j < je; ++j, bit <<= 1) {
     const float4 pj = __ldg(&pos4[j]);
     float dx, dy, dz;
