@@ -306,6 +306,20 @@ def test_fp32_pairs_match_fp64():
     assert d.max() < RC_R
 
 
+def test_fp32_pairs_subset_matches_full():
+    """The per-atom subset form (used on large frames) gives the same rows,
+    on a periodic box and on a slab open along z."""
+    rng = np.random.default_rng(5)
+    for box in (np.array([15.1, 19.0, 19.0], np.float32), np.array([20.0, 19.0, 0.0], np.float32)):
+        ext = np.where(box > 0, box, 15.0)
+        pos = (rng.random((400, 3)) * ext).astype(np.float32)
+        full = oracle.neighbours_fp32(pos, box, RC_R)
+        atoms = rng.choice(len(pos), size=50, replace=False)
+        sub = oracle.neighbours_fp32(pos, box, RC_R, atoms=atoms)
+        for a, row in zip(atoms, sub):
+            assert np.array_equal(row, full[a])
+
+
 # ------------------------------------------------------------------ spectra
 def test_acf_matches_fft_wiener_khinchin():
     rng = np.random.default_rng(3)
