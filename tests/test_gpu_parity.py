@@ -155,17 +155,23 @@ def test_device_and_host_inputs_agree(tn):
 
 
 def test_batch_split_is_bitwise_invariant(tn):
-    """Results do not depend on how frames are grouped into device passes."""
-    frames, types, box = synth.water_small(9)
+    """Results do not depend on how frames are grouped into device passes,
+    for a box with too few cells for shifts (12.42 A) and one scanned with
+    x-thin cells and windows (24.84 A, 1,536 atoms)."""
+    rng = np.random.default_rng(21)
+    base, btypes, bbox = synth.water_grid_box(8, 24.84, rng)
+    bframes = synth.random_walk_frames(base, bbox, 6, 0.05, rng).astype(np.float32)
+    cases = (synth.water_small(9), (bframes, btypes, bbox.astype(np.float32)))
     ms, _ = models_for(tn, 2)
     ctx = tn.tnep_create(ms, 2, RC)
-    outs = []
-    for fb in (1, 4, 9):
-        tn.tnep_set_option(ctx, tn.TNEP_OPT_FRAMES_PER_BATCH, fb)
-        outs.append(tn.tnep_eval(ctx, frames, box, types))
-    for o in outs[1:]:
-        for a, b in zip(outs[0], o):
-            assert np.array_equal(a, b)
+    for frames, types, box in cases:
+        outs = []
+        for fb in (1, 4, len(frames)):
+            tn.tnep_set_option(ctx, tn.TNEP_OPT_FRAMES_PER_BATCH, fb)
+            outs.append(tn.tnep_eval(ctx, frames, box, types))
+        for o in outs[1:]:
+            for a, b in zip(outs[0], o):
+                assert np.array_equal(a, b)
     ctx.close()
 
 
