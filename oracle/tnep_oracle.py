@@ -546,16 +546,17 @@ def acf(series, max_lag=None, kind=KIND_IR, subtract_mean=True):
     return np.array([np.einsum("tab,tba->", beta[:T - t], beta[t:]) / (T - t) for t in range(M + 1)])
 
 
-def spectrum(series, dt_fs, kind=KIND_IR, max_lag=None, subtract_mean=True):
+def spectrum(series, dt_fs, kind=KIND_IR, max_lag=None, subtract_mean=True, k_sel=None):
     """One-sided cosine transform of the ACF.
 
     S(nu_k) = dt [C(0) + 2 sum_{tau=1}^{M} C(tau) cos(2 pi nu_k tau dt)],
     nu_k = k / (2 M dt), k = 0..M.  IR is multiplied by omega^2 (Eq. 6).
-    Returns (frequency in cm^-1, spectrum).
+    Returns (frequency in cm^-1, spectrum); with k_sel, only the rows k in
+    k_sel (same formula, for lags too long to hold the full M x M table).
     """
     C = acf(series, max_lag, kind, subtract_mean)
     M = len(C) - 1
-    k = np.arange(M + 1)
+    k = np.arange(M + 1) if k_sel is None else np.asarray(k_sel, dtype=np.int64)
     tau = np.arange(1, M + 1)
     nu = k / (2.0 * M * dt_fs) if M > 0 else np.zeros(1)
     S = dt_fs * (C[0] + 2.0 * (C[1:][None, :] * np.cos(np.pi * np.outer(k, tau) / max(M, 1))).sum(1))

@@ -29,13 +29,17 @@ tnep_status noalloc_fail(tnep_status s, const char* msg) {
   return s;
 }
 
-bool on_device(const void* p) {
+// True for device memory of device `dev` and for managed memory.  Device
+// memory of another GPU is refused: the kernels run on the current device
+// and would reach it through a peer address, which faults without peer access.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -57,13 +61,14 @@ extern "C" tnep_status tnep_spectrum_noalloc(const double* series, int T, int C,
   }
   const int M = max_lag <= 0 ? T / 2 : max_lag;
   if (M < 1 || M >= T) return noalloc_fail(TNEP_ERR_INVALID, "max_lag must be in [1, T)");
-  if (!on_device(series) || !on_device(freq_cm1) || !on_device(spec) || (acf_out && !on_device(acf_out)))
-    return noalloc_fail(TNEP_ERR_INVALID, "series and outputs must be device memory");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return noalloc_fail(TNEP_ERR_NO_DEVICE, "no current CUDA device");
   }
+  if (!on_device(series, dev) || !on_device(freq_cm1, dev) || !on_device(spec, dev) ||
+      (acf_out && !on_device(acf_out, dev)))
+    return noalloc_fail(TNEP_ERR_INVALID, "series and outputs must be memory of the current device");
   double* scratch = nullptr;
   {
     // Set-up once per device, with that device current: the host-side name

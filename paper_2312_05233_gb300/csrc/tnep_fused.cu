@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
         }
         tc::commit_to(mbar);
       }
-      const bool ok = tc::mbar_wait_bounded(mbar, parity, kMbarTries);
+      // every thread polls the mbarrier itself; the barrier-and makes the
+      // give-up decision the same for the whole CTA
+      const bool ok = __syncthreads_and(tc::mbar_wait_bounded(mbar, parity, kMbarTries)) != 0;
       tc::fence_after_sync();
       return ok;
     };
@@ -416,24 +418,52 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
 #pragma unroll
     for (int d = 0; d < 32; ++d) buf[d] = d < DP ? q[d] * sc[d] : 0.f;
     write_row(buf);
+    // Give-up path: when a product's completion does not arrive in time, the
+    // CTA reads no TMEM, rewrites no operand tile and issues no further
+    // product (an unfinished product may still read the tile and write its
+    // columns).  It raises TNEP_ERR_TIMEOUT, waits once more (bounded) for
+    // that completion, frees its columns only if it arrived -- a late write
+    // can then never land in columns that another CTA has since been given
+    // -- and returns without storing a result.  If the completion never
+    // arrives, the CTA exits with its columns still allocated rather than
+    // free columns a product may still write; the host gets TNEP_ERR_TIMEOUT.
+    uint32_t pending = 0;  // parity of the product whose completion is awaited
     bool ok = gemm(tileB1, 0);
     float z[32];
+    if (ok) {
 #pragma unroll
-    for (int k = 0; k < 32; ++k) z[k] = 0.f;
-    read_row(z);
+      for (int k = 0; k < 32; ++k) z[k] = 0.f;
+      read_row(z);
 #pragma unroll
-    for (int h = 0; h < 32; ++h) {
-      if (h < Ly.H) {
-        const float hh = tanhf(z[h] - b0[h]);
-        const float wh = w1[h];
-        U += wh * hh;
-        buf[h] = wh * (1.f - hh * hh);
-      } else {
-        buf[h] = 0.f;
+      for (int h = 0; h < 32; ++h) {
+        if (h < Ly.H) {
+          const float hh = tanhf(z[h] - b0[h]);
+          const float wh = w1[h];
+          U += wh * hh;
+          buf[h] = wh * (1.f - hh * hh);
+        } else {
+          buf[h] = 0.f;
+        }
       }
+      // the first product has completed, so the A tile may be rewritten; its
+      // TMEM columns are rewritten only by the second product, which is
+      // issued after the CTA-wide barrier in gemm, i.e. after every warp's
+      // tcgen05.ld (each followed by tcgen05.wait::ld) above
+      write_row(buf);
+      pending = 1;
+      ok = gemm(tileB2, 1);
     }
-    write_row(buf);
-    ok = gemm(tileB2, 1) && ok;
+    if (!ok) {
+      if (tid == 0 && a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
+      const bool drained = __syncthreads_and(tc::mbar_wait_bounded(mbar, pending, kMbarTries)) != 0;
+      if (drained) {
+        tc::fence_after_sync();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < 32; ++k) z[k] = 0.f;
     read_row(z);
@@ -442,7 +472,6 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     tc::fence_before_sync();
     __syncthreads();
     if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
-    if (!ok && a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
   } else if constexpr (FACT) {
     // scalar products: measured faster than the packed form below in the
     // factored population kernel

@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtnep.so")
 
 TNEP_OK = 0
+TNEP_ERR_INVALID = 1
 STATUS_NAMES = {
     0: "TNEP_OK", 1: "TNEP_ERR_INVALID", 2: "TNEP_ERR_OOM", 3: "TNEP_ERR_BOX_TOO_SMALL",
     4: "TNEP_ERR_NEIGHBOR_OVERFLOW", 5: "TNEP_ERR_CUDA", 6: "TNEP_ERR_TIMEOUT",
@@ -408,12 +409,34 @@ def tnep_spectrum_noalloc(series, dt_fs: float, kind: int, freq_out, spec_out, a
                           subtract_mean=True, stream=None):
     """Device series [T][C] -> fills the device tensors freq_out, spec_out (and acf_out).
 
-    Asynchronous on `stream`; uses the library's static scratch (no allocation)."""
+    Asynchronous on `stream`; uses the library's static scratch (no allocation).
+    The C entry point cannot see buffer lengths, so this wrapper checks them
+    before the call: series must be a contiguous 2-D float64 CUDA tensor (no
+    converted temporary, which could be freed while the call still reads it),
+    and every output a contiguous float64 tensor on the same device with at
+    least M + 1 elements, M = max_lag or T // 2."""
+    import torch
+    if not isinstance(series, torch.Tensor) or series.dim() != 2:
+        raise TnepError(TNEP_ERR_INVALID, "series must be a 2-D [T][C] tensor")
+    if series.dtype != torch.float64 or not series.is_contiguous():
+        raise TypeError("series must be a contiguous torch.float64 tensor")
+    Tn, Cn = int(series.shape[0]), int(series.shape[1])
+    M = Tn // 2 if max_lag <= 0 else int(max_lag)
+    outs = [("freq_out", freq_out), ("spec_out", spec_out)] + ([("acf_out", acf_out)] if acf_out is not None else [])
+    for name, t in outs:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.numel() < M + 1:
+            raise TnepError(TNEP_ERR_INVALID, f"{name} holds {t.numel()} elements, needs M + 1 = {M + 1}")
+    if series.device.type != "cuda":
+        raise TnepError(TNEP_ERR_INVALID, "series must be a CUDA tensor")
+    for name, t in outs:
+        if t.device != series.device:
+            raise TnepError(TNEP_ERR_INVALID, f"{name} is on {t.device}, series on {series.device}")
     S = _Buf(series, np.float64, "series")
     F = _Buf(freq_out, np.float64, "freq_out", writable=True)
     P = _Buf(spec_out, np.float64, "spec_out", writable=True)
     A = _Buf(acf_out, np.float64, "acf_out", writable=True)
-    Tn, Cn = int(series.shape[0]), int(series.shape[1])
     _check(_lib.tnep_spectrum_noalloc(S.ptr, Tn, Cn, float(dt_fs), int(kind), int(max_lag),
                                       int(bool(subtract_mean)), F.ptr, P.ptr, A.ptr, _stream_ptr(stream)))
 

@@ -129,3 +129,32 @@ def test_raman_validation(tn):
     assert lib.tnep_raman_porto_map(L.ctypes.data, 5, 1, v.ctypes.data, 3, f.ctypes.data, f.ctypes.data,
                                     None) == 1
     assert "axis" in lib.tnep_last_error().decode()
+
+
+def test_noalloc_wrapper_checks_buffers_before_any_call(tn):
+    """The C entry point cannot see buffer lengths, so the binding checks
+    them: outputs shorter than M + 1, a series that is not 2-D, not float64
+    or not contiguous, and a series not in CUDA memory are all refused before
+    the library is called (CPU tensors here: nothing reaches a device)."""
+    import torch
+    s = torch.zeros((100, 3), dtype=torch.float64)
+    ok = torch.zeros(51, dtype=torch.float64)
+    short = torch.zeros(50, dtype=torch.float64)
+    with pytest.raises(tn.TnepError) as e:
+        tn.tnep_spectrum_noalloc(s, 1.0, tn.TNEP_SPECTRUM_IR, short, ok)
+    assert e.value.status == 1 and "freq_out" in str(e.value)
+    with pytest.raises(tn.TnepError) as e:
+        tn.tnep_spectrum_noalloc(s, 1.0, tn.TNEP_SPECTRUM_IR, ok, ok, short)
+    assert e.value.status == 1 and "acf_out" in str(e.value)
+    with pytest.raises(tn.TnepError) as e:  # max_lag 70 needs 71 elements
+        tn.tnep_spectrum_noalloc(s, 1.0, tn.TNEP_SPECTRUM_IR, ok, ok, max_lag=70)
+    assert e.value.status == 1 and "71" in str(e.value)
+    with pytest.raises(tn.TnepError):
+        tn.tnep_spectrum_noalloc(s.reshape(-1), 1.0, tn.TNEP_SPECTRUM_IR, ok, ok)
+    with pytest.raises(TypeError):
+        tn.tnep_spectrum_noalloc(s.float(), 1.0, tn.TNEP_SPECTRUM_IR, ok, ok)
+    with pytest.raises(TypeError):
+        tn.tnep_spectrum_noalloc(torch.zeros((3, 100), dtype=torch.float64).t(), 1.0, tn.TNEP_SPECTRUM_IR, ok, ok)
+    with pytest.raises(tn.TnepError) as e:  # sizes fine, but host memory
+        tn.tnep_spectrum_noalloc(s, 1.0, tn.TNEP_SPECTRUM_IR, ok, ok)
+    assert e.value.status == 1 and "CUDA" in str(e.value)

@@ -457,3 +457,17 @@ def test_lattice_translations_of_single_atoms_change_nothing():
     moved[17] += H[0] + H[1] + H[2]
     got = oracle.evaluate(m, moved, None, types, cell=H)
     np.testing.assert_allclose(got.per_atom, ref.per_atom, atol=1e-10 * np.abs(ref.per_atom).max())
+
+
+def test_spectrum_row_selection_equals_full_rows():
+    """oracle.spectrum(k_sel=...) returns the selected rows of the full
+    transform (used where the full M x M cosine table would not fit)."""
+    rng = np.random.default_rng(3)
+    s = rng.normal(size=(300, 9))
+    for kind in (oracle.KIND_IR, oracle.KIND_RAMAN_ANISO):
+        ser = s[:, :3] if kind == oracle.KIND_IR else s
+        f, S = oracle.spectrum(ser, 0.5, kind, max_lag=120)
+        ks = np.array([0, 3, 77, 120])
+        fk, Sk = oracle.spectrum(ser, 0.5, kind, max_lag=120, k_sel=ks)
+        assert np.array_equal(fk, f[ks])
+        np.testing.assert_allclose(Sk, S[ks], rtol=1e-14, atol=1e-14 * np.abs(S).max())
