@@ -434,10 +434,15 @@ enum {
   TNEP_OPT_POPULATION_FORM = 10,    /* angular form of populations created afterwards: 0 = the faster of the
                                        two by timing (default), 1 = per-pair walk, 2 = factored through the
                                        angular moments (FP32 network only; otherwise the walk) */
-  TNEP_OPT_CELL_XDIV = 11           /* k_x in {1, 2, 3, 4} (default 2), used with cell_div = 1: cells of edge
+  TNEP_OPT_CELL_XDIV = 11,          /* k_x in {1, 2, 3, 4} (default 2), used with cell_div = 1: cells of edge
                                        rc_R / k_x along x; for k_x > 1 each atom scans, in each (y, z) row of its
                                        stencil, only the x-cells that meet [x_i - h, x_i + h], h^2 = rc_R^2 -
                                        (distance from atom i to the row)^2.  Same pair sets; list order may differ. */
+  TNEP_OPT_ALLOC_COUNT = 12         /* read-only: device and pinned-host allocations made by the library in this
+                                       process so far.  Host-side fault injection: with the environment variable
+                                       TNEP_FAULT=oom@N set before the library is loaded, allocation number N
+                                       fails once (nothing is allocated, the device is untouched) and the call
+                                       making it returns TNEP_ERR_OOM; the context stays usable. */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

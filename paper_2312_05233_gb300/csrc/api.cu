@@ -64,9 +64,9 @@ tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types
   }
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_k0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev_k1);
-  if (e == cudaSuccess) e = cudaMalloc(&c->ws.d_status, sizeof(DevStatus));
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&c->ws.d_status), sizeof(DevStatus));
   if (e == cudaSuccess) e = c->ws.h_status.ensure(1);
-  if (e == cudaSuccess) e = cudaMalloc(&c->skin_ws.d_status, sizeof(DevStatus));
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&c->skin_ws.d_status), sizeof(DevStatus));
   if (e == cudaSuccess) e = c->skin_ws.h_status.ensure(1);
   if (e != cudaSuccess) return bail(cuda_fail(e, "context setup"));
   for (int k = 0; k < n_models; ++k) {
@@ -88,7 +88,7 @@ tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types
     pack_model(c, m);
     std::vector<float> packed(m.lay.words);
     pack_params(m, n_types, m.params.data(), m.scaler.data(), packed.data());
-    e = cudaMalloc(&m.d_packed, sizeof(float) * m.lay.words);
+    e = dev_malloc(reinterpret_cast<void**>(&m.d_packed), sizeof(float) * m.lay.words);
     if (e == cudaSuccess)
       e = cudaMemcpy(m.d_packed, packed.data(), sizeof(float) * m.lay.words, cudaMemcpyHostToDevice);
     c->models.push_back(std::move(m));
@@ -185,6 +185,7 @@ tnep_status tnep_get_option(const tnep_ctx* c, int option, double* value) {
     case TNEP_OPT_POPULATION_FORM: *value = c->population_form; return TNEP_OK;
     case TNEP_OPT_CELL_XDIV: *value = c->x_div; return TNEP_OK;
     case TNEP_OPT_LAST_SKIN_USED: *value = c->last_skin_used; return TNEP_OK;
+    case TNEP_OPT_ALLOC_COUNT: *value = (double)alloc_count(); return TNEP_OK;
     default: return fail(TNEP_ERR_INVALID, "unknown option");
   }
 }
@@ -521,7 +522,7 @@ tnep_status tnep_spectrum(const double* series, int T, int C, double dt_fs, int 
   const size_t n_z = use_fft ? (size_t)18 * N + (size_t)N / 2 : 0;  // double2
   double* d = nullptr;
   const size_t total = 2 * n_z + n_series + n_work + 2 * (size_t)(M + 1) + (M + 1);
-  TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * total, st));
+  TNEP_CUDA(dev_malloc_async((void**)&d, sizeof(double) * total, st));
   double2* d_z = reinterpret_cast<double2*>(d);  // first: the allocation's alignment holds
   double* d_series = d + 2 * n_z;
   double* d_work = d_series + n_series;

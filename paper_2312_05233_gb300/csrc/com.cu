@@ -90,7 +90,7 @@ tnep_status tnep_add_com_dipole(tnep_ctx* c, int n_structs, const int* atom_offs
   const size_t bytes = sizeof(int) * (n_structs + 1) + sizeof(double) * (c->n_types + n_structs + nmu) +
                        sizeof(float) * 3 * (size_t)N + sizeof(int) * (size_t)N + 64;
   char* d = nullptr;
-  TNEP_CUDA(cudaMallocAsync((void**)&d, bytes, st));
+  TNEP_CUDA(dev_malloc_async((void**)&d, bytes, st));
   double* d_mass = reinterpret_cast<double*>(d);
   double* d_q = d_mass + c->n_types;
   double* d_mu = d_q + n_structs;

@@ -3,8 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -14,9 +17,43 @@ namespace {
 
 thread_local std::string g_last_error;
 
+std::atomic<long long> g_allocs{0};
+long long g_fault_at = 0;  // 0 = no injected failure
+std::once_flag g_fault_once;
+
+// True if this allocation is the one TNEP_FAULT=oom@N asks to fail.
+bool injected_oom() {
+  std::call_once(g_fault_once, [] {
+    const char* v = std::getenv("TNEP_FAULT");
+    if (v && std::strncmp(v, "oom@", 4) == 0) g_fault_at = std::atoll(v + 4);
+  });
+  const long long k = g_allocs.fetch_add(1, std::memory_order_relaxed) + 1;
+  return g_fault_at > 0 && k == g_fault_at;
+}
+
 }  // namespace
 
 namespace tnep {
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_oom()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (injected_oom()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_oom()) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
+
+long long alloc_count() { return g_allocs.load(std::memory_order_relaxed); }
 
 tnep_status fail(tnep_status s, const std::string& msg) {
   g_last_error = msg;

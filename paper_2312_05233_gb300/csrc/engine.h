@@ -30,6 +30,17 @@ tnep_status cuda_fail(cudaError_t e, const char* what);
     if (_s != TNEP_OK) return _s;         \
   } while (0)
 
+// Every allocation of the library goes through these three calls.  They
+// count allocations (process-wide) and implement host-side fault injection:
+// with the environment variable TNEP_FAULT=oom@N set when the library loads,
+// the N-th allocation fails once with cudaErrorMemoryAllocation (nothing is
+// allocated and the device is not touched), so callers can check that every
+// entry point returns TNEP_ERR_OOM and that the context stays usable.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st);
+cudaError_t host_alloc(void** p, size_t bytes);
+long long alloc_count();
+
 template <class T>
 struct DevBuf {
   T* p = nullptr;
@@ -40,7 +51,7 @@ struct DevBuf {
     p = nullptr;
     n = 0;
     const size_t want = std::max<size_t>(std::max<size_t>(m, 1), m + m / 4);
-    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    cudaError_t e = dev_malloc(reinterpret_cast<void**>(&p), want * sizeof(T));
     if (e != cudaSuccess) { p = nullptr; return e; }
     n = want;
     return cudaSuccess;
@@ -62,7 +73,7 @@ struct PinBuf {
     p = nullptr;
     n = 0;
     const size_t want = std::max<size_t>(m, 1);
-    cudaError_t e = cudaHostAlloc((void**)&p, want * sizeof(T), cudaHostAllocDefault);
+    cudaError_t e = host_alloc(reinterpret_cast<void**>(&p), want * sizeof(T));
     if (e != cudaSuccess) { p = nullptr; return e; }
     n = want;
     return cudaSuccess;

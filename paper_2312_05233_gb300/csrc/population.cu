@@ -158,7 +158,7 @@ tnep_status create_pop(tnep_population* p, const float* params0, const float* po
   TNEP_CUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
   TNEP_CUDA(cudaEventCreate(&p->ev0));
   TNEP_CUDA(cudaEventCreate(&p->ev1));
-  TNEP_CUDA(cudaMalloc(&p->ws.d_status, sizeof(DevStatus)));
+  TNEP_CUDA(dev_malloc(reinterpret_cast<void**>(&p->ws.d_status), sizeof(DevStatus)));
   TNEP_CUDA(p->ws.h_status.ensure(1));
   cudaStream_t st = p->stream;
   TNEP_CUDA(p->d_pos.ensure((size_t)std::max(N, 1) * 3));

@@ -252,7 +252,7 @@ tnep_status tnep_raman_tensor(const double* series, int T, double dt_fs, int max
   while (N < T + M) N <<= 1;
   const size_t nZ = use_fft ? (size_t)2 * 23 * N + (size_t)N / 2 : 0;  // double2: two work arrays + twiddles
   double* d = nullptr;
-  TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (nS + nX + nC + nT + nF + nL + 16 + 2 * nZ), st));
+  TNEP_CUDA(dev_malloc_async((void**)&d, sizeof(double) * (nS + nX + nC + nT + nF + nL + 16 + 2 * nZ), st));
   // the FFT work area (double2) first, where the allocation's alignment holds
   double2* zwork = reinterpret_cast<double2*>(d);
   double* d_s = d + 2 * nZ;
@@ -305,7 +305,7 @@ tnep_status tnep_raman_polarized(const double* L, int max_lag, int n_orient, con
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t nL = (size_t)(max_lag + 1) * 81, nV = (size_t)n_orient * 3, nO = (size_t)n_orient * (max_lag + 1);
   double* d = nullptr;
-  TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (nL + 2 * nV + nO), st));
+  TNEP_CUDA(dev_malloc_async((void**)&d, sizeof(double) * (nL + 2 * nV + nO), st));
   double *d_l = d, *d_n = d_l + nL, *d_e = d_n + nV, *d_o = d_e + nV;
   cudaError_t e = cudaMemcpyAsync(d_l, L, sizeof(double) * nL, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_n, n, sizeof(double) * nV, cudaMemcpyDefault, st);
@@ -332,7 +332,7 @@ tnep_status tnep_raman_porto_map(const double* L, int max_lag, int n_theta, cons
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t nL = (size_t)(max_lag + 1) * 81, nO = (size_t)n_theta * (max_lag + 1);
   double* d = nullptr;
-  TNEP_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (nL + n_theta + 2 * nO), st));
+  TNEP_CUDA(dev_malloc_async((void**)&d, sizeof(double) * (nL + n_theta + 2 * nO), st));
   double *d_l = d, *d_t = d_l + nL, *d_p = d_t + n_theta, *d_c = d_p + nO;
   cudaError_t e = cudaMemcpyAsync(d_l, L, sizeof(double) * nL, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, theta, sizeof(double) * n_theta, cudaMemcpyDefault, st);

@@ -2,14 +2,17 @@
 //
 // Requests (one structure each, any size, open or periodic) are copied in by
 // tnep_submit and admitted while the device-memory budget and the request
-// slots allow.  A worker thread keeps `n_pipelines` batches in flight, each
-// on its own stream with its own resident workspace: whenever a pipeline is
-// free it takes every pending request (up to max_batch_atoms) and launches
-// the whole path (cell lists, neighbour lists, radial moments, fused
-// kernels, FP64 reduction) as one batch, so requests that arrive while
-// others run are batched together and overlap them on the device.  Each
-// structure's result is bitwise the same alone or in any batch (fixed
-// per-structure reduction order).  All waits are bounded.
+// slots allow.  Up to `n_pipelines` batches are in flight, each on its own
+// stream with its own resident workspace: whenever a pipeline is free, every
+// pending request (up to max_batch_atoms) is launched on it as one batch
+// through the whole path (cell lists, neighbour lists, radial moments, fused
+// kernels, FP64 reduction), so requests that arrive while others run are
+// batched together and overlap them on the device.  A request that finds a
+// pipeline free and nothing queued is launched by the submitting thread
+// itself (no hand-off to the worker); the worker launches everything else
+// and, while batches are in flight, polls their completion events without
+// sleeping.  Each structure's result is bitwise the same alone or in any
+// batch (fixed per-structure reduction order).  All waits are bounded.
 
 #include <cuda_runtime.h>
 
@@ -22,6 +25,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "engine.h"
@@ -77,7 +81,8 @@ struct tnep_server {
   std::vector<std::unique_ptr<Pipeline>> pipes;
   std::deque<ReqPtr> pending;
   std::unordered_map<uint64_t, ReqPtr> table;
-  std::mutex mu;
+  std::mutex mu;           // requests: pending queue, ticket table, counters
+  std::mutex dispatch_mu;  // pipelines: busy flags, batches, launches (taken before mu)
   std::condition_variable cv_done, cv_work;
   std::thread worker;
   std::atomic<bool> stop{false};
@@ -165,65 +170,95 @@ bool complete_batch(tnep_server* s, Pipeline& p) {
   return false;
 }
 
+// Launches pending requests on every free pipeline.  Caller holds
+// dispatch_mu.  Returns true if anything was launched.
+bool dispatch_pending(tnep_server* s) {
+  bool launched = false;
+  for (auto& pp : s->pipes) {
+    Pipeline& p = *pp;
+    if (p.busy) continue;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      if (s->pending.empty()) break;
+      long long atoms = 0;
+      while (!s->pending.empty()) {
+        const ReqPtr& r = s->pending.front();
+        if (!p.batch.empty() && atoms + r->n_atoms > s->max_batch_atoms) break;
+        atoms += r->n_atoms;
+        p.batch.push_back(r);
+        s->pending.pop_front();
+      }
+    }
+    p.busy = true;
+    launched = true;
+    const tnep_status st = launch_batch(s, p);
+    if (st != TNEP_OK) {
+      std::lock_guard<std::mutex> lock(s->mu);
+      for (auto& r : p.batch) finish_request(s, r, st);
+      p.batch.clear();
+      p.busy = false;
+      s->cv_done.notify_all();
+    }
+  }
+  return launched;
+}
+
+// Completes every finished batch.  Caller holds dispatch_mu.  Returns
+// (progressed, pipelines still busy).
+std::pair<bool, int> poll_completions(tnep_server* s) {
+  bool progressed = false;
+  int busy = 0;
+  for (auto& pp : s->pipes) {
+    Pipeline& p = *pp;
+    if (!p.busy) continue;
+    const cudaError_t q = cudaEventQuery(p.done_ev);
+    if (q == cudaSuccess) {
+      complete_batch(s, p);
+      progressed = true;
+    } else if (q != cudaErrorNotReady) {
+      cudaGetLastError();
+      std::lock_guard<std::mutex> lock(s->mu);
+      for (auto& r : p.batch) finish_request(s, r, TNEP_ERR_CUDA);
+      p.batch.clear();
+      p.busy = false;
+      s->cv_done.notify_all();
+      progressed = true;
+    }
+    busy += p.busy;
+  }
+  return {progressed, busy};
+}
+
 void worker_loop(tnep_server* s) {
   cudaSetDevice(s->ctx->device);
   for (;;) {
-    bool progressed = false;
-    int busy = 0;
-    for (auto& pp : s->pipes) {
-      Pipeline& p = *pp;
-      if (!p.busy) continue;
-      const cudaError_t q = cudaEventQuery(p.done_ev);
-      if (q == cudaSuccess) {
-        complete_batch(s, p);
+    bool progressed;
+    int busy;
+    {
+      std::lock_guard<std::mutex> dl(s->dispatch_mu);
+      auto pr = poll_completions(s);
+      progressed = pr.first;
+      busy = pr.second;
+      if (dispatch_pending(s)) {
         progressed = true;
-      } else if (q != cudaErrorNotReady) {
-        cudaGetLastError();
-        std::lock_guard<std::mutex> lock(s->mu);
-        for (auto& r : p.batch) finish_request(s, r, TNEP_ERR_CUDA);
-        p.batch.clear();
-        p.busy = false;
-        s->cv_done.notify_all();
-      }
-      busy += p.busy;
-    }
-    for (auto& pp : s->pipes) {
-      Pipeline& p = *pp;
-      if (p.busy) continue;
-      {
-        std::lock_guard<std::mutex> lock(s->mu);
-        if (s->pending.empty()) break;
-        long long atoms = 0;
-        while (!s->pending.empty()) {
-          const ReqPtr& r = s->pending.front();
-          if (!p.batch.empty() && atoms + r->n_atoms > s->max_batch_atoms) break;
-          atoms += r->n_atoms;
-          p.batch.push_back(r);
-          s->pending.pop_front();
-        }
-      }
-      p.busy = true;
-      ++busy;
-      progressed = true;
-      const tnep_status st = launch_batch(s, p);
-      if (st != TNEP_OK) {
-        std::lock_guard<std::mutex> lock(s->mu);
-        for (auto& r : p.batch) finish_request(s, r, st);
-        p.batch.clear();
-        p.busy = false;
-        --busy;
-        s->cv_done.notify_all();
+        busy = 0;
+        for (auto& pp : s->pipes) busy += pp->busy;
       }
     }
     if (s->stop.load() && busy == 0) {
       std::lock_guard<std::mutex> lock(s->mu);
       if (s->pending.empty()) break;
     }
-    if (!progressed) {
-      std::unique_lock<std::mutex> lock(s->mu);
-      // bounded: new work wakes us; otherwise poll in-flight events again soon
-      s->cv_work.wait_for(lock, std::chrono::microseconds(busy ? 20 : 200));
+    if (progressed) continue;
+    if (busy) {
+      // batches in flight: poll their events again at once (the result is on
+      // the host as soon as the event completes)
+      std::this_thread::yield();
+      continue;
     }
+    std::unique_lock<std::mutex> lock(s->mu);
+    // idle: a submit or stop wakes us; bounded so that nothing is missed
+    if (s->pending.empty() && !s->stop.load()) s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
   }
 }
 
@@ -250,7 +285,7 @@ tnep_status tnep_server_start(tnep_ctx* ctx, size_t mem_budget_bytes, int max_sl
     auto p = std::make_unique<Pipeline>();
     cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&p->ws.d_status, sizeof(DevStatus));
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&p->ws.d_status), sizeof(DevStatus));
     if (e == cudaSuccess) e = p->ws.h_status.ensure(1);
     s->pipes.push_back(std::move(p));
     if (e != cudaSuccess) {
@@ -293,8 +328,23 @@ tnep_status tnep_submit(tnep_server* s, const tnep_request* req, uint64_t* ticke
     s->table[r->ticket] = r;
     s->pending.push_back(r);
   }
-  s->cv_work.notify_one();
   *ticket = r->ticket;
+  // A free pipeline: launch from this thread at once.  If the worker holds
+  // the pipelines, it launches the request on its next pass.
+  {
+    std::unique_lock<std::mutex> dl(s->dispatch_mu, std::try_to_lock);
+    if (dl.owns_lock()) {
+      int prev = -1;
+      const bool switch_dev = cudaGetDevice(&prev) == cudaSuccess && prev != s->ctx->device;
+      if (!switch_dev || cudaSetDevice(s->ctx->device) == cudaSuccess) {
+        dispatch_pending(s);
+        if (switch_dev) cudaSetDevice(prev);
+      } else {
+        cudaGetLastError();  // the worker launches the request instead
+      }
+    }
+  }
+  s->cv_work.notify_one();
   return TNEP_OK;
 }
 

@@ -612,16 +612,26 @@ def test_population_factored_form(tn, rank, small, n_types):
 
 
 # ------------------------------------------------- tensor-core network
-# Mode 1 rounds activations and weights to BF16 (relative error up to 2^-8
-# per product).  The weight rounding is shared by every atom, so the per-atom
-# errors can add coherently: the bound is 2^-8 times the condition scale
-# sum_i |c_i|.  Mode 2 splits both operands into high and low BF16 parts
-# (three products, omitted term ~2^-18) and is held to the FP32 tolerance.
-U_BF16 = 2.0 ** -8
+# Mode 1 rounds activations and weights to BF16 (unit roundoff 2^-9) with
+# FP32 accumulation.  The bar is the BF16 tolerance of 1e-3, taken on the
+# tensor, ||dT|| <= 1e-3 ||T||, or, for a tensor that is a cancelling sum, on
+# its condition scale sum_i |c_i| (the sum over atoms and components of the
+# absolute per-atom contributions): ||dT|| <= 1e-3 sum_i |c_i|.  The
+# condition-scale fallback keeps the same 1e-3 (not 1e-4 as for FP32, where
+# per-atom rounding is independent): the rounding of the per-type weights is
+# shared by every atom, and on near-crystalline structures the rounding of
+# the activations is nearly the same for every atom of a type, so per-atom
+# errors add coherently.  Largest measured: 6.3e-4 of the condition scale
+# (3x3x3 BaZrO3, rank 2, small model), 9.6e-4 of sum_i ||c_i|| and
+# 9e-3 of ||mu|| (64-molecule water, where mu cancels).
+# Mode 2 splits both operands into high and low BF16 parts (three products,
+# omitted term ~2^-18) and is held to the FP32 tolerance.
+BF16_REL = 1e-3
+BF16_COND = 1e-3
 
 
 def bf16_bound(r):
-    return U_BF16 * np.abs(r.per_atom).sum()
+    return max(BF16_REL * np.linalg.norm(r.tensor), BF16_COND * np.abs(r.per_atom).sum())
 
 
 def with_precision(tn, ms, mode, n_types):
@@ -655,6 +665,29 @@ def test_tensor_core_network(tn, small, n_types):
             assert np.linalg.norm(outs[2][k][f] - r.tensor) <= max(REL * scale, COND * cond)
         assert not np.array_equal(outs[1][k], outs[0][k])  # the tensor-core paths really ran
         assert not np.array_equal(outs[2][k], outs[1][k])
+
+
+def test_tensor_core_network_perovskite_full_size(tn):
+    """BaZrO3 12x12x12 (8,640 atoms, 3 types), rank-2 susceptibility, the
+    precision workload: whole frames through the oracle.  BF16 network (mode
+    1): relative Frobenius error <= 1e-3 per frame, each component within
+    1e-3 of the tensor's norm; split BF16 (mode 2) and FP32 (mode 0): 1e-5."""
+    frames, types, box = synth.bzo_perovskite(n_frames=3)
+    rng = np.random.default_rng(synth.seed_for(3, 1))
+    hp = synth.HyperParams(n_types=3, rank=2)
+    p = synth.model_params(hp, rng)
+    sc = synth.default_q_scaler(hp)
+    om = oracle.OracleModel.from_flat(hp, p, sc, *RC)
+    refs = [oracle.evaluate(om, frames[f], box, types).tensor for f in (0, 2)]
+    bars = {0: 1e-5, 1: 1e-3, 2: 1e-5}
+    for mode in (0, 1, 2):
+        ctx = tn.tnep_create([tn.Model.from_hyper(hp, p, sc, mlp_precision=mode)], 3, RC)
+        (al,) = tn.tnep_eval(ctx, frames, box, types)
+        ctx.close()
+        for got, ref in zip(al[[0, 2]], refs):
+            nrm = np.linalg.norm(ref)
+            assert np.linalg.norm(got - ref) <= bars[mode] * nrm, (mode, np.linalg.norm(got - ref) / nrm)
+            assert np.all(np.abs(got - ref) <= bars[mode] * nrm), mode
 
 
 def test_tensor_core_population_and_tail_block(tn):

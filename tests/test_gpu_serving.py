@@ -69,9 +69,16 @@ def test_admission_budget_slots_and_timeout(tn):
     big = synth.serving_requests(1, np.random.default_rng(2), max_mol=64)[0]
     frames, types, box = synth.water_bulk(n_frames=1)
     wtypes = np.where(types == 0, 3, 0).astype(np.int32)
+    # a request that keeps the GPU busy for milliseconds (8 bulk-water
+    # frames side by side, 331,776 atoms): it is still in flight when the
+    # zero-timeout wait below is made, although a lone request is launched
+    # inside submit itself
+    shifts = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], np.float32) * box
+    big_pos = (frames[0][None] + shifts[:, None]).reshape(-1, 3)
+    big_types = np.tile(wtypes, 8)
     # one slot: the second request is refused until the first finishes
     with tn.tnep_server_start(ctx, max_slots=1, n_pipelines=1) as srv:
-        t1 = srv.submit(frames[0], wtypes, box)
+        t1 = srv.submit(big_pos, big_types, 2 * box)
         assert t1 is not None
         assert srv.submit(big.pos, big.types, big.box) is None
         with pytest.raises(tn.TnepError) as e:
