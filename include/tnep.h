@@ -208,13 +208,15 @@ tnep_status tnep_population_create(tnep_ctx* ctx, int model, int n_pop, const fl
 /* Replays the captured generation for new parameters [n_pop][n_params] (host):
  * rmse [n_pop], out NULL or [n_pop][n_structs][C] (host).  Synchronous. */
 tnep_status tnep_population_eval(tnep_population* pop, const float* params, double* rmse, double* out);
-/* info[13]: atoms per CTA, CTA order and form chosen (0 = per-pair angular
- * walk, 1 = factored through the angular moments), the eight timed candidates
- * (ms per generation: walk with 128/atom-major, 128/individual-major,
- * 64/atom-major, 64/individual-major, then the factored form in the same
- * order; -1 = not applicable), last generation's device time (ms), atoms in
- * the structure set. */
-tnep_status tnep_population_info(const tnep_population* pop, double info[13]);
+/* info[14]: atoms per CTA, CTA order and form chosen (0 = per-pair angular
+ * walk, 1 = factored through the angular moments on the CUDA cores, 2 =
+ * factored with tensor-core products), the eight timed candidates of the
+ * first two forms (ms per generation: walk with 128/atom-major,
+ * 128/individual-major, 64/atom-major, 64/individual-major, then the
+ * factored form in the same order; -1 = not applicable), last generation's
+ * device time (ms), atoms in the structure set, the timed tensor-core form
+ * (ms, -1 = not applicable). */
+tnep_status tnep_population_info(const tnep_population* pop, double info[14]);
 void tnep_population_destroy(tnep_population* pop);
 
 /* ---- Training loop: separable natural evolution strategy (Sec. II.D) ----
@@ -431,9 +433,12 @@ enum {
                                        every pass with lists built per frame.  Results agree with s = 0 to float32
                                        rounding (pair order may differ). */
   TNEP_OPT_LAST_SKIN_USED = 9,      /* read-only: 1 if the last tnep_eval used skin lists in every pass */
-  TNEP_OPT_POPULATION_FORM = 10,    /* angular form of populations created afterwards: 0 = the faster of the
-                                       two by timing (default), 1 = per-pair walk, 2 = factored through the
-                                       angular moments (FP32 network only; otherwise the walk) */
+  TNEP_OPT_POPULATION_FORM = 10,    /* angular form of populations created afterwards: 0 = the fastest by
+                                       timing (default), 1 = per-pair walk, 2 = factored through the angular
+                                       moments on the CUDA cores, 3 = factored with the angular sums and the
+                                       angular share of Eqs. 3-4 as tensor-core products over the individuals
+                                       (2 and 3: FP32 network only; 3: standard descriptor sizes and at most 3
+                                       types; otherwise the fastest available) */
   TNEP_OPT_CELL_XDIV = 11,          /* k_x in {1, 2, 3, 4} (default 2), used with cell_div = 1: cells of edge
                                        rc_R / k_x along x; for k_x > 1 each atom scans, in each (y, z) row of its
                                        stencil, only the x-cells that meet [x_i - h, x_i + h], h^2 = rc_R^2 -

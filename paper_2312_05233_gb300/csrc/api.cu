@@ -162,7 +162,8 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       c->skin = (float)value;
       return TNEP_OK;
     case TNEP_OPT_POPULATION_FORM:
-      if (value != 0.0 && value != 1.0 && value != 2.0) return fail(TNEP_ERR_INVALID, "population form must be 0, 1 or 2");
+      if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+        return fail(TNEP_ERR_INVALID, "population form must be 0, 1, 2 or 3");
       c->population_form = (int)value;
       return TNEP_OK;
     default:

@@ -1,0 +1,487 @@
+// Population evaluation with the angular contractions on the tensor cores.
+//
+// Sec. II.D: the evolution strategy evaluates a population of parameter
+// vectors on the training structures every generation.  g^A_n is linear in
+// the angular coefficients c, so for a centre atom i of type tau and an
+// individual p (angmom.cu holds the per-atom moments B and Phi / Psi):
+//   A_{p,n,lm}(i)    = sum_{(t,k)} c^{tau t}_{p,n,k} B^t_{k,lm}(i)
+// and the angular share of Eqs. 3-4, with G = dU/dA and
+// H^t_{k,lm} = sum_n G_nlm c_nk, is
+//   -sum_{t,k,lm} H^t_{k,lm} Phi^t_{k,lm,c}(i) = -sum_n sum_lm G_{p,n,lm} X_{p,n,lm,c}(i),
+//   X_{p,n,lm,c}(i)  = sum_{(t,k)} c^{tau t}_{p,n,k} Phi^t_{k,lm,c}(i).
+// Both A and X are dense products with the same left operand
+// C[(p, n)][(t, k)] (one 128-row tile holds 25 individuals x 5 orders n;
+// K = T * 9 <= 32) and the atoms' moments as the right operand: rows (i, lm)
+// for A, rows (lm, c) for X.  They run as tcgen05.mma (kind::f16, BF16
+// operands, FP32 accumulation in TMEM).  For FP32 accuracy every operand is
+// split into three BF16 terms, x = x1 + x2 + x3 (|x - x1 - x2 - x3| <= 2^-24
+// |x|), and the six products whose order is <= 2 are accumulated
+// (x1 y1, x1 y2, x2 y1, x1 y3, x2 y2, x3 y1; the rest is below 2^-24).
+//
+// One CTA (128 threads) takes one tile of 5 atoms of one centre type and 25
+// individuals.  TMEM lane r = 5 p + n holds row (p, n).
+//   1. bulk copies (cp.async.bulk, mbarrier) of the coefficient tile and of
+//      the 5 atoms' B blocks into shared memory; one product A for all 5
+//      atoms (N = 128 columns); lane (p, n) reads its A_{n,lm}(i) and forms
+//      q_nl and the 4-body term of its n for each atom.
+//   2. thread (p, i): radial descriptor from the radial moments, the FP32
+//      network (Eq. 1), dU/dq and the radial part of Eqs. 3-4.
+//   3. per atom (and, for rank 2, per third of its lm): the product A again
+//      (N = 32) and X (N = 80) from a double-buffered bulk copy of the Phi
+//      block; lane (p, n) forms G_{n,lm} and its partial contraction; thread
+//      (p, i) sums the five n in a fixed order and writes the per-atom
+//      tensor.
+// Each structure's per-atom results depend only on its atoms, so the usual
+// FP64 per-structure reduction follows.  All waits are bounded; on give-up
+// the CTA raises TNEP_ERR_TIMEOUT, issues nothing further, waits (bounded)
+// for what it has in flight, frees TMEM only if that arrived and stores
+// nothing.
+
+#include <cuda_bf16.h>
+
+#include "tc_sm100.cuh"
+#include "tnep_device.cuh"
+#include "tnep_internal.cuh"
+
+namespace tnep {
+
+namespace {
+
+constexpr int kPT = kPopTcIndividuals;  // individuals per 128-row tile (125 rows used)
+constexpr int kNT = kPopTcAtoms;        // atoms per CTA
+constexpr int kKW = 96;                 // bf16 per operand row: three terms x K = 32
+constexpr int kGroup = 8 * kKW * 2;     // bytes of 8 rows
+constexpr int kBBytes = 3 * kGroup;     // one atom's B block: 24 rows (lm)
+constexpr int kChunkRows = 72;          // rows of one X product (lm, c)
+constexpr int kChunkBytes = 9 * kGroup;
+constexpr int kCoefBytes = 16 * kGroup;  // 128 rows
+constexpr long long kTries = 1LL << 22;
+
+// smem layout (bytes)
+constexpr int kOffC = 0;
+constexpr int kOffB = kOffC + kCoefBytes;              // 16 groups: 5 atoms x 3 + one pad group
+constexpr int kOffX0 = kOffB + 16 * kGroup;            // 10 groups: 72 rows + 8 pad
+constexpr int kOffX1 = kOffX0 + 10 * kGroup;
+constexpr int kOffQ = kOffX1 + 10 * kGroup;            // float [25][5][32] (later the n-sums)
+constexpr int kOffE = kOffQ + kPT * kNT * 32 * 4;      // float [25][5][32]
+constexpr int kOffBar = kOffE + kPT * kNT * 32 * 4;    // 4 mbarriers + TMEM slot
+constexpr int kSmemBytes = kOffBar + 64;
+
+__device__ __forceinline__ uint32_t tile_off(int row, int part, int k) {
+  return tc::kmajor_offset(row, part * 32 + k, kKW);
+}
+
+// x = x1 + x2 + x3 in BF16; each residual is exact in FP32.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16* t) {
+  t[0] = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(t[0]);
+  t[1] = __float2bfloat16_rn(r1);
+  t[2] = __float2bfloat16_rn(r1 - __bfloat162float(t[1]));
+}
+
+// Writes one operand row (32 K values, three terms) in the canonical layout.
+__device__ __forceinline__ void store_row(unsigned char* tile, int row, const float* v) {
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+    __nv_bfloat16 h[3][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      __nv_bfloat16 t[3];
+      split3(v[8 * kc + u], t);
+      h[0][u] = t[0]; h[1][u] = t[1]; h[2][u] = t[2];
+    }
+#pragma unroll
+    for (int part = 0; part < 3; ++part)
+      *reinterpret_cast<uint4*>(tile + tile_off(row, part, 8 * kc)) = *reinterpret_cast<const uint4*>(h[part]);
+  }
+}
+
+// Per-atom moment blocks in the tensor-core layout: B (24 rows lm), then Phi
+// (rank 1) or Psi (rank 2) (24 * C rows (lm, c)); K = (t, k), zero beyond T * 9.
+// Atom n_atoms is an all-zero block (padding of partial tiles).
+__global__ void __launch_bounds__(128) k_moments_tc(int n_atoms, int T, int C, const float* __restrict__ amom,
+                                                    int amom_slots, unsigned char* __restrict__ dst,
+                                                    size_t stride) {
+  const int rows = 24 + 24 * C;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)(n_atoms + 1) * rows) return;
+  const int a = (int)(g / rows), row = (int)(g % rows);
+  const int GBP = pad4(24 * C);
+  float v[32];
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) {
+    const int t = kk / 9, k = kk % 9;
+    float x = 0.f;
+    if (a < n_atoms && t < T) {
+      const int slot = row < 24 ? (t * 9 + k) * 24 + row : T * 9 * 24 + (t * 9 + k) * GBP + (row - 24);
+      x = amom[amom_index(a, slot, amom_slots)];
+    }
+    v[kk] = x;
+  }
+  unsigned char* blk = dst + (size_t)a * stride;
+  if (row < 24) store_row(blk, row, v);
+  else store_row(blk + kBBytes, row - 24, v);
+}
+
+// Per generation: the left operand C[(p, n)][(t, k)] of every (centre type,
+// individual tile), rows p * 5 + n (zero beyond the population and K).
+__global__ void __launch_bounds__(128) k_coef_tc(int n_pop, int T, int n_mt, const float* __restrict__ params,
+                                                 int words, int off_cA, int stride_cA, unsigned char* __restrict__ dst) {
+  const int tau = blockIdx.x / n_mt, mt = blockIdx.x % n_mt;
+  const int r = threadIdx.x;
+  const int pl = r / 5, n = r % 5, p = mt * kPT + pl;
+  const bool valid = r < kPT * 5 && p < n_pop;
+  float v[32];
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) {
+    const int t = kk / 9, k = kk % 9;
+    v[kk] = (valid && t < T) ? params[(size_t)p * words + off_cA + (tau * T + t) * stride_cA + n * 9 + k] : 0.f;
+  }
+  store_row(dst + (size_t)blockIdx.x * kCoefBytes, r, v);
+}
+
+// Issues the six split products of one K = 32 operand pair into `d`.
+__device__ __forceinline__ void issue_split_products(uint32_t d, uint32_t a_base, uint32_t b_base, uint32_t idesc) {
+  const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+  int step = 0;
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int q = 0; q < 6; ++q, ++step)
+      tc::mma_bf16(d, tc::smem_desc(a_base + 512 * pa[q] + 256 * ks, 128, kGroup),
+                   tc::smem_desc(b_base + 512 * pb[q] + 256 * ks, 128, kGroup), idesc, step > 0);
+}
+
+template <int RANK>
+__global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTcArgs a) {
+  constexpr int C = RANK == 1 ? 3 : 9;
+  constexpr int NCH = RANK == 1 ? 1 : 3;  // X products per atom (72 rows each)
+  constexpr int NR = 5, NA = 5, BR = 9, NLM = 24, DP = 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* qbuf = reinterpret_cast<float*>(smem + kOffQ);
+  float* ebuf = reinterpret_cast<float*>(smem + kOffE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffBar + 32);
+  const uint32_t s_base = tc::smem_addr(smem);
+  const uint32_t bar_load = tc::smem_addr(&bars[0]), bar_mma = tc::smem_addr(&bars[1]);
+  const uint32_t bar_x[2] = {tc::smem_addr(&bars[2]), tc::smem_addr(&bars[3])};
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tile = blockIdx.x / a.n_mt, mt = blockIdx.x % a.n_mt;
+  const int* td = a.tiles + (size_t)tile * 8;
+  const int tau = td[5], count = td[6];
+  const int pl = tid / 5, x = tid % 5;            // (individual, n) in phases 1 and 3; (individual, atom) in 2
+  const int p = mt * kPT + pl;
+  const bool prow = tid < kPT * 5 && p < a.n_pop;  // a real (individual, .) row
+  const int T = a.n_types;
+  const size_t xs = a.mom_tc_stride;
+  auto atom_of = [&](int i) { return td[i]; };      // a.n_atoms (zero block) for empty slots
+  auto x_src = [&](int q) {
+    const int i = q / NCH, j = q % NCH;
+    return a.mom_tc + (size_t)atom_of(i) * xs + kBBytes + (size_t)j * kChunkBytes;
+  };
+
+  // ---------------------------------------------------------------- set-up
+  if (tid == 0) {
+    for (int b = 0; b < 4; ++b) tc::mbar_init(tc::smem_addr(&bars[b]), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), 128);
+  // pad groups (never read into a result column, zeroed all the same)
+  for (int k = tid; k < kGroup / 16; k += 128) {
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(smem + kOffB + 15 * kGroup)[k] = z;
+    reinterpret_cast<uint4*>(smem + kOffX0 + 9 * kGroup)[k] = z;
+    reinterpret_cast<uint4*>(smem + kOffX1 + 9 * kGroup)[k] = z;
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+
+  const int n_chunks = kNT * NCH;
+  // issued by thread 0 and not yet observed complete (for the give-up path)
+  int n_commit = 0, x_issued[2] = {0, 0}, x_seen[2] = {0, 0};
+  bool load_seen = false;
+  volatile int* s_flag = reinterpret_cast<volatile int*>(smem + kOffBar + 36);
+  if (tid == 0) {
+    tc::mbar_expect_tx(bar_load, kCoefBytes + kNT * kBBytes);
+    tc::bulk_g2s(s_base + kOffC, a.coef_tc + (size_t)(tau * a.n_mt + mt) * kCoefBytes, kCoefBytes, bar_load);
+    for (int i = 0; i < kNT; ++i)
+      tc::bulk_g2s(s_base + kOffB + i * kBBytes, a.mom_tc + (size_t)atom_of(i) * xs, kBBytes, bar_load);
+    tc::mbar_expect_tx(bar_x[0], kChunkBytes);
+    tc::bulk_g2s(s_base + kOffX0, x_src(0), kChunkBytes, bar_x[0]);
+    x_issued[0] = 1;
+  }
+
+  // ---------------------------------------------------------------- 1. A for all atoms, q_nl
+  bool ok = true;
+  int mma_done = 0;  // completions of bar_mma observed by every thread
+  if (tid == 0) {
+    ok = load_seen = tc::mbar_wait_bounded(bar_load, 0, kTries);
+    if (ok) {
+      tc::fence_after_sync();
+      issue_split_products(tmem, s_base + kOffC, s_base + kOffB, tc::idesc_bf16_f32(128, 128));
+      tc::commit_to(bar_mma);
+      ++n_commit;
+    }
+  }
+  ok = __syncthreads_and(ok && tc::mbar_wait_bounded(bar_mma, 0, kTries)) != 0;
+  if (!ok) goto give_up;
+  mma_done = 1;
+  tc::fence_after_sync();
+#pragma unroll 1
+  for (int i = 0; i < kNT; ++i) {
+    float A[32];
+    tc::tmem_ld32(lane_base + i * 24, A);
+    if (prow) {
+      float* qd = qbuf + (pl * kNT + i) * 32;
+#pragma unroll
+      for (int l = 1; l <= 4; ++l) {
+        float s = 0.f;
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm)
+          if (l_of(lm) == l) s += wlm(lm) * A[lm] * A[lm];
+        qd[NR + (l - 1) * NA + x] = s;
+      }
+      float gr[5];
+      qd[NR + 4 * NA + x] = kC4 * trace_m3(&A[3], gr);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+
+  // ---------------------------------------------------------------- 2. network (Eq. 1), radial part
+  {
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+    float U = 0.f;
+    const bool mine = prow && x < count;  // thread (p, atom x)
+    if (mine) {
+      const int atom = atom_of(x);
+      const ModelLayout& Ly = a.lay;
+      const float* model = a.params + (size_t)p * Ly.words;
+      const float* cR_i = model + Ly.off_cR + tau * T * Ly.stride_cR;
+      const float* mom = a.mom + atom;
+      float q[DP];
+#pragma unroll
+      for (int d = 0; d < DP; ++d) q[d] = 0.f;
+      for (int t = 0; t < T; ++t) {
+        float Fk[BR];
+#pragma unroll
+        for (int k = 0; k < BR; ++k) Fk[k] = mom[(size_t)(t * kMomBasis + k) * a.mom_stride];
+        const float* cc = cR_i + t * Ly.stride_cR;
+#pragma unroll
+        for (int n = 0; n < NR; ++n)
+#pragma unroll
+          for (int k = 0; k < BR; ++k) q[n] += __ldg(cc + n * BR + k) * Fk[k];
+      }
+      const float* qd = qbuf + (pl * kNT + x) * 32;
+#pragma unroll
+      for (int d = NR; d < 30; ++d) q[d] = qd[d];
+      const int net = Ly.nets > 1 ? tau : 0;
+      const float* W0 = model + Ly.off_W0 + net * Ly.H * DP;
+      const float* b0 = model + Ly.off_b0 + net * Ly.H;
+      const float* w1 = model + Ly.off_w1 + net * Ly.H;
+      const float* sc = model + Ly.off_scaler;
+      float s[DP], e[DP];
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        s[d] = d < 30 ? q[d] * __ldg(sc + d) : 0.f;
+        e[d] = 0.f;
+      }
+      U = -__ldg(model + Ly.off_b1 + net);
+      for (int h = 0; h < Ly.H; ++h) {
+        const float4* row = reinterpret_cast<const float4*>(W0 + h * DP);
+        float z = -__ldg(b0 + h);
+#pragma unroll
+        for (int v = 0; v < DP / 4; ++v) {
+          const float4 w = __ldg(row + v);
+          z += w.x * s[4 * v] + w.y * s[4 * v + 1] + w.z * s[4 * v + 2] + w.w * s[4 * v + 3];
+        }
+        const float hh = tanhf(z);
+        const float wh = __ldg(w1 + h);
+        U += wh * hh;
+        const float vh = wh * (1.f - hh * hh);
+#pragma unroll
+        for (int v = 0; v < DP / 4; ++v) {
+          const float4 w = __ldg(row + v);
+          e[4 * v] += vh * w.x; e[4 * v + 1] += vh * w.y; e[4 * v + 2] += vh * w.z; e[4 * v + 3] += vh * w.w;
+        }
+      }
+      float* ed = ebuf + (pl * kNT + x) * 32;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        e[d] *= d < 30 ? __ldg(sc + d) : 0.f;
+        ed[d] = e[d];
+      }
+      // radial part of Eqs. 3-4 through the moments V (rank 1) or W (rank 2)
+      for (int t = 0; t < T; ++t) {
+        const float* cc = cR_i + t * Ly.stride_cR;
+#pragma unroll
+        for (int k = 0; k < BR; ++k) {
+          float Dk = 0.f;
+#pragma unroll
+          for (int n = 0; n < NR; ++n) Dk += e[n] * __ldg(cc + n * BR + k);
+          const int tk = t * kMomBasis + k;
+          if constexpr (RANK == 1) {
+            const float* v = mom + (size_t)(a.v0 + 3 * tk) * a.mom_stride;
+            acc[0] -= Dk * v[0];
+            acc[1] -= Dk * v[(size_t)a.mom_stride];
+            acc[2] -= Dk * v[2 * (size_t)a.mom_stride];
+          } else {
+            const float* w = mom + (size_t)(a.w0 + 6 * tk) * a.mom_stride;
+            const size_t ms = a.mom_stride;
+            const float wxx = w[0], wxy = w[ms], wxz = w[2 * ms], wyy = w[3 * ms], wyz = w[4 * ms], wzz = w[5 * ms];
+            acc[0] -= Dk * wxx; acc[1] -= Dk * wxy; acc[2] -= Dk * wxz;
+            acc[3] -= Dk * wxy; acc[4] -= Dk * wyy; acc[5] -= Dk * wyz;
+            acc[6] -= Dk * wxz; acc[7] -= Dk * wyz; acc[8] -= Dk * wzz;
+          }
+        }
+      }
+      if constexpr (RANK == 2) { acc[0] += U; acc[4] += U; acc[8] += U; }
+    }
+    __syncthreads();  // ebuf complete; qbuf free for the n-sums
+
+    // -------------------------------------------------------------- 3. per atom: A again, X, contraction
+    float G[NLM], part[C];
+#pragma unroll 1
+    for (int i = 0; i < kNT; ++i) {
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int q = i * NCH + j, b = q & 1;
+        bool ok0 = true;
+        if (tid == 0) {
+          ok0 = tc::mbar_wait_bounded(bar_x[b], (q >> 1) & 1, kTries);
+          if (ok0) {
+            ++x_seen[b];
+            // the other buffer's last product has completed: refill it
+            if (q + 1 < n_chunks) {
+              tc::mbar_expect_tx(bar_x[b ^ 1], kChunkBytes);
+              tc::bulk_g2s(s_base + (b ? kOffX0 : kOffX1), x_src(q + 1), kChunkBytes, bar_x[b ^ 1]);
+              ++x_issued[b ^ 1];
+            }
+            tc::fence_after_sync();
+            if (j == 0)
+              issue_split_products(tmem, s_base + kOffC, s_base + kOffB + 3 * i * kGroup,
+                                   tc::idesc_bf16_f32(128, 32));
+            issue_split_products(tmem + 32, s_base + kOffC, s_base + (b ? kOffX1 : kOffX0),
+                                 tc::idesc_bf16_f32(128, 80));
+            tc::commit_to(bar_mma);
+            ++n_commit;
+          }
+        }
+        ok = __syncthreads_and(ok0 && tc::mbar_wait_bounded(bar_mma, mma_done & 1, kTries)) != 0;
+        if (!ok) goto give_up;
+        ++mma_done;
+        tc::fence_after_sync();
+        if (j == 0) {
+          float Av[32];
+          tc::tmem_ld32(lane_base, Av);
+          const float* ed = ebuf + (pl * kNT + i) * 32;
+#pragma unroll
+          for (int lm = 0; lm < NLM; ++lm)
+            G[lm] = prow ? 2.f * wlm(lm) * ed[NR + (l_of(lm) - 1) * NA + x] * Av[lm] : 0.f;
+          if (prow) {
+            float gr[5];
+            trace_m3(&Av[3], gr);
+            const float e4 = kC4 * ed[NR + 4 * NA + x];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) G[3 + m] += e4 * gr[m];
+          }
+#pragma unroll
+          for (int c = 0; c < C; ++c) part[c] = 0.f;
+        }
+        // X column 32 + f, f = lm' * C + c with lm = (72 / C) j + lm'
+#pragma unroll
+        for (int blk = 0; blk < 3; ++blk) {
+          float Xv[32];
+          tc::tmem_ld32(lane_base + 32 + 32 * blk, Xv);
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const int f = 32 * blk + u;
+            if (f < kChunkRows) part[f % C] += G[(kChunkRows / C) * j + f / C] * Xv[u];
+          }
+        }
+        float* red = qbuf + (i & 1) * (kPT * 5 * C);
+        if (j == NCH - 1 && prow) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) red[(pl * 5 + x) * C + c] = part[c];
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (j == NCH - 1 && mine && x == i) {
+          float* out = a.per_atom + (size_t)p * a.per_atom_stride + atom_of(i);
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            float sum = 0.f;
+#pragma unroll
+            for (int n = 0; n < 5; ++n) sum += red[(pl * 5 + n) * C + c];
+            out[(size_t)c * a.atom_stride] = acc[c] - sum;
+          }
+        }
+      }
+    }
+  }
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  return;
+
+give_up:
+  // Nothing further is issued.  Thread 0 knows what it started: the bulk
+  // loads, the last committed product, and an X copy per buffer.  It waits
+  // (bounded) for each of them; TMEM is freed only if all arrived, so no late
+  // product can write columns another CTA has been given since.
+  if (tid == 0) {
+    if (a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
+    bool drained = true;
+    if (!load_seen) drained = tc::mbar_wait_bounded(bar_load, 0, kTries) && drained;
+    if (n_commit > mma_done) drained = tc::mbar_wait_bounded(bar_mma, (n_commit - 1) & 1, kTries) && drained;
+    for (int b = 0; b < 2; ++b)
+      if (x_issued[b] > x_seen[b]) drained = tc::mbar_wait_bounded(bar_x[b], (x_issued[b] - 1) & 1, kTries) && drained;
+    *s_flag = drained ? 1 : 0;
+  }
+  __syncthreads();
+  if (*s_flag) {
+    tc::fence_after_sync();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+}  // namespace
+
+size_t pop_tc_moment_stride(int rank) { return (size_t)kBBytes + (size_t)(rank == 1 ? 1 : 3) * kChunkBytes; }
+size_t pop_tc_coef_bytes() { return kCoefBytes; }
+
+cudaError_t launch_moments_tc(int n_atoms, int n_types, int rank, const float* amom, int amom_slots,
+                              unsigned char* dst, cudaStream_t st) {
+  const int C = rank == 1 ? 3 : 9;
+  const long long threads = (long long)(n_atoms + 1) * (24 + 24 * C);
+  count_launches(1);
+  k_moments_tc<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_atoms, n_types, C, amom, amom_slots, dst,
+                                                                  pop_tc_moment_stride(rank));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_tc(int n_pop, int n_types, int n_mt, const float* params, const ModelLayout& lay,
+                           unsigned char* dst, cudaStream_t st) {
+  count_launches(1);
+  k_coef_tc<<<n_types * n_mt, 128, 0, st>>>(n_pop, n_types, n_mt, params, lay.words, lay.off_cA, lay.stride_cA, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pop_tc(int rank, const PopTcArgs& a, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  count_launches(1);
+  auto fn = rank == 1 ? k_pop_tc<1> : k_pop_tc<2>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)a.n_tiles * a.n_mt, 128, kSmemBytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tnep

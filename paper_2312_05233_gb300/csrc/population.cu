@@ -39,9 +39,14 @@ struct tnep_population {
   PinBuf<double> h_rmse, h_pred;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int block = 128, pop_major = 0, fact = 0;
+  int block = 128, pop_major = 0, fact = 0;  // fact: 0 walk, 1 factored (CUDA cores), 2 factored (tensor cores)
   bool fact_ok = false;          // angular moments available
   DevBuf<float> amom;            // angular moments (factored form)
+  bool tc_ok = false;            // tensor-core form available (pop_tc.cu)
+  DevBuf<unsigned char> mom_tc, coef_tc;
+  DevBuf<int> tc_tiles;
+  int n_tiles = 0, n_mt = 0;
+  double tc_ms = -1.0;
   double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double last_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -73,7 +78,32 @@ tnep_status enqueue_generation(tnep_population* p, bool with_copies) {
     TNEP_CUDA(cudaMemcpyAsync(p->d_params.p, p->h_params.p, sizeof(float) * (size_t)p->n_pop * m.lay.words,
                               cudaMemcpyHostToDevice, st));
   FusedArgs f = pop_args(p);
-  TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, p->n_pop, p->block, m.d.mlp_precision, st));
+  if (p->fact == 2) {
+    TNEP_CUDA(launch_coef_tc(p->n_pop, p->ctx->n_types, p->n_mt, p->d_params.p, m.lay, p->coef_tc.p, st));
+    PopTcArgs t{};
+    t.n_tiles = p->n_tiles;
+    t.n_mt = p->n_mt;
+    t.n_pop = p->n_pop;
+    t.n_types = p->ctx->n_types;
+    t.n_atoms = p->N;
+    t.tiles = p->tc_tiles.p;
+    t.mom_tc = p->mom_tc.p;
+    t.mom_tc_stride = pop_tc_moment_stride(m.d.rank);
+    t.coef_tc = p->coef_tc.p;
+    t.params = p->d_params.p;
+    t.lay = m.lay;
+    t.mom = f.mom;
+    t.mom_stride = f.mom_stride;
+    t.v0 = f.v0;
+    t.w0 = f.w0;
+    t.per_atom = f.per_atom;
+    t.per_atom_stride = f.per_atom_stride;
+    t.atom_stride = f.atom_stride;
+    t.status = f.status;
+    TNEP_CUDA(launch_pop_tc(m.d.rank, t, st));
+  } else {
+    TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, p->n_pop, p->block, m.d.mlp_precision, st));
+  }
   TNEP_CUDA(launch_reduce(p->S, p->n_pop, p->ws.offsets.p, p->ws.max_atoms, p->ws.per_atom.p, f.per_atom_stride,
                           p->ws.atom_stride, m.C, p->ws.partial.p, p->d_pred.p, (size_t)p->S * m.C, st));
   TNEP_CUDA(launch_rmse(p->n_pop, p->S, m.C, p->d_pred.p, p->d_target.p, p->d_rmse.p, st));
@@ -128,9 +158,63 @@ tnep_status autotune(tnep_population* p) {
       }
     }
   }
+  // the tensor-core form (one launch shape)
+  p->tc_ms = -1.0;
+  const int form = p->ctx->population_form;
+  if (p->tc_ok && (form == 0 || form == 3)) {
+    p->fact = 2;
+    TNEP_TRY(enqueue_generation(p, false));  // warm-up
+    TNEP_CUDA(cudaEventRecord(p->ev0, p->stream));
+    for (int r = 0; r < 3; ++r) TNEP_TRY(enqueue_generation(p, false));
+    TNEP_CUDA(cudaEventRecord(p->ev1, p->stream));
+    TNEP_CUDA(cudaEventSynchronize(p->ev1));
+    float ms = 0.f;
+    TNEP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    p->tc_ms = ms / 3.0;
+    if (ms < best || form == 3) { best = ms; best_f = 2; }
+  }
   p->block = best_b;
   p->pop_major = best_o;
   p->fact = best_f;
+  return TNEP_OK;
+}
+
+// Tiles of the tensor-core form: the atoms of each centre type in sorted
+// order, kPopTcAtoms per tile (the zero block, index N, fills the last one),
+// and the per-atom moment blocks in the layout the products read.
+tnep_status setup_tc(tnep_population* p) {
+  const Model& m = p->ctx->models[p->model];
+  const int N = p->N, T = p->ctx->n_types;
+  std::vector<float4> pos4(N);
+  TNEP_CUDA(cudaMemcpyAsync(pos4.data(), p->ws.pos4.p, sizeof(float4) * N, cudaMemcpyDeviceToHost, p->stream));
+  TNEP_CUDA(cudaStreamSynchronize(p->stream));
+  std::vector<int> tiles;
+  for (int t = 0; t < T; ++t) {
+    std::vector<int> at;
+    for (int i = 0; i < N; ++i) {
+      int ti;
+      std::memcpy(&ti, &pos4[i].w, sizeof(int));
+      if (ti == t) at.push_back(i);
+    }
+    for (size_t k = 0; k < at.size(); k += kPopTcAtoms) {
+      int rec[8] = {N, N, N, N, N, t, 0, 0};
+      const int cnt = (int)std::min<size_t>(kPopTcAtoms, at.size() - k);
+      for (int u = 0; u < cnt; ++u) rec[u] = at[k + u];
+      rec[6] = cnt;
+      tiles.insert(tiles.end(), rec, rec + 8);
+    }
+  }
+  p->n_tiles = (int)tiles.size() / 8;
+  p->n_mt = (p->n_pop + kPopTcIndividuals - 1) / kPopTcIndividuals;
+  if ((long long)p->n_tiles * p->n_mt > 0x7fffffffLL) return fail(TNEP_ERR_UNSUPPORTED, "too many tiles");
+  TNEP_CUDA(p->tc_tiles.ensure(std::max<size_t>(tiles.size(), 1)));
+  TNEP_CUDA(cudaMemcpyAsync(p->tc_tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice,
+                            p->stream));
+  TNEP_CUDA(p->mom_tc.ensure((size_t)(N + 1) * pop_tc_moment_stride(m.d.rank)));
+  TNEP_CUDA(p->coef_tc.ensure((size_t)T * p->n_mt * pop_tc_coef_bytes()));
+  const int slots = (int)angular_moment_slots(m.variant, m.d.rank, T);
+  TNEP_CUDA(launch_moments_tc(N, T, m.d.rank, p->amom.p, slots, p->mom_tc.p, p->stream));
+  TNEP_CUDA(cudaStreamSynchronize(p->stream));
   return TNEP_OK;
 }
 
@@ -146,6 +230,7 @@ void destroy_pop(tnep_population* p) {
   p->d_pos.release(); p->d_box.release(); p->d_types.release(); p->d_params.release(); p->h_params.release();
   p->d_target.release(); p->d_rmse.release(); p->d_pred.release(); p->h_rmse.release(); p->h_pred.release();
   p->amom.release();
+  p->mom_tc.release(); p->coef_tc.release(); p->tc_tiles.release();
   if (p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -205,6 +290,18 @@ tnep_status create_pop(tnep_population* p, const float* params0, const float* po
     } else {
       cudaGetLastError();
       p->amom.release();
+    }
+  }
+  // tensor-core form: standard descriptor, <= 3 types, FP32 network; without
+  // the memory for its moment blocks the other forms are used
+  if (p->fact_ok && m.variant == kVarStd && c->n_types <= 3 && m.d.mlp_precision == 0 &&
+      (c->population_form == 0 || c->population_form == 3)) {
+    const tnep_status ts = setup_tc(p);
+    p->tc_ok = ts == TNEP_OK;
+    if (!p->tc_ok) {
+      cudaGetLastError();
+      p->mom_tc.release(); p->coef_tc.release(); p->tc_tiles.release();
+      if (ts != TNEP_ERR_OOM) return ts;
     }
   }
   const size_t pa = (size_t)m.C * p->ws.atom_stride * p->n_pop;
@@ -295,7 +392,7 @@ tnep_status tnep_population_eval(tnep_population* p, const float* params, double
   return TNEP_OK;
 }
 
-tnep_status tnep_population_info(const tnep_population* p, double info[13]) {
+tnep_status tnep_population_info(const tnep_population* p, double info[14]) {
   if (!p || !info) return fail(TNEP_ERR_INVALID, "NULL argument");
   info[0] = p->block;
   info[1] = p->pop_major;
@@ -303,6 +400,7 @@ tnep_status tnep_population_info(const tnep_population* p, double info[13]) {
   for (int k = 0; k < 8; ++k) info[3 + k] = p->tune_ms[k];
   info[11] = p->last_ms;
   info[12] = p->N;
+  info[13] = p->tc_ms;
   return TNEP_OK;
 }
 

@@ -71,6 +71,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar_saddr, uint32_t pari
   return ok != 0;
 }
 
+// Arrives on the mbarrier and adds `bytes` to the transaction count its
+// current phase waits for (the issuing thread, before its bulk copies).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar_saddr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_saddr), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> shared (the async proxy, no tensor map): `bytes` a
+// multiple of 16, both addresses 16-byte aligned; completion is counted on
+// the mbarrier in bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void* src, uint32_t bytes, uint32_t mbar_saddr) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst_saddr),
+      "l"(src), "r"(bytes), "r"(mbar_saddr)
+      : "memory");
+}
+
 // Waits for the phase with the given parity, giving up after `max_tries`
 // attempts (each try_wait may itself suspend briefly).  Returns false on
 // give-up.

@@ -39,19 +39,6 @@ namespace tnep {
 
 namespace {
 
-// (2 2 2; 0 0 0) = -sqrt(2/35);  C4 = -sqrt(2/35) * (5/(4 pi))^1.5 * 9/2
-constexpr float kC4 = -0.26998130975990770f;
-
-// Addition-theorem weights of the real polynomials, l = 1..4 (see real_harmonics):
-// w = (4 pi / (2l+1)) * (normalisation of the orthonormal real harmonic)^2.
-constexpr float wlm(int k) {
-  constexpr float w[24] = {1.f, 1.f, 1.f, 3.f, 3.f, 3.f, 0.75f, 0.25f, 0.625f, 15.f, 0.375f, 0.25f,
-                           0.375f, 3.75f, 0.625f, 8.75f, 4.375f, 1.25f, 0.625f, 0.015625f, 0.625f,
-                           0.3125f, 4.375f, 0.546875f};
-  return w[k];
-}
-constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : (k < 15 ? 3 : 4)); }
-
 // V += sum_lm S_lm * grad p_lm(x, y, z)  (gradient of the polynomial as written).
 // Each order l accumulates into its own partial sums so that the four
 // dependency chains run side by side.
@@ -104,29 +91,6 @@ __device__ __forceinline__ void load_coeffs(const float* blk, float* cc) {
     const float4 t = c4[v];
     cc[4 * v] = t.x; cc[4 * v + 1] = t.y; cc[4 * v + 2] = t.z; cc[4 * v + 3] = t.w;
   }
-}
-
-// Tr(M^3) of the traceless symmetric M built from the l=2 sums a[0..4]
-// (xy, yz, xz, x^2-y^2, 3z^2-1), and its gradient with respect to a.
-__device__ __forceinline__ float trace_m3(const float* a, float* grad) {
-  const float mxy = a[0], myz = a[1], mxz = a[2];
-  const float mzz = a[4] * (1.f / 3.f);
-  const float mxx = 0.5f * (a[3] - mzz), myy = 0.5f * (-a[3] - mzz);
-  const float nxx = mxx * mxx + mxy * mxy + mxz * mxz;
-  const float nyy = mxy * mxy + myy * myy + myz * myz;
-  const float nzz = mxz * mxz + myz * myz + mzz * mzz;
-  const float nxy = mxx * mxy + mxy * myy + mxz * myz;
-  const float nyz = mxy * mxz + myy * myz + myz * mzz;
-  const float nxz = mxx * mxz + mxy * myz + mxz * mzz;
-  // Tr(M^3) = sum_ij M_ij (M^2)_ji
-  const float tr = mxx * nxx + myy * nyy + mzz * nzz + 2.f * (mxy * nxy + myz * nyz + mxz * nxz);
-  // d Tr(M^3) = 3 Tr(M^2 dM)
-  grad[0] = 6.f * nxy;
-  grad[1] = 6.f * nyz;
-  grad[2] = 6.f * nxz;
-  grad[3] = 1.5f * (nxx - nyy);
-  grad[4] = nzz - 0.5f * (nxx + nyy);
-  return tr;
 }
 
 // Bytes of shared memory the tensor-core network needs after the scratch:

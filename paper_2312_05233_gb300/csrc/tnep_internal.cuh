@@ -193,6 +193,32 @@ __host__ __device__ inline size_t amom_index(int i, int s, int n_slots) {
 size_t angular_moment_slots(int variant, int rank, int n_types);
 cudaError_t launch_angular_moments(int variant, int rank, const AngMomArgs& a, cudaStream_t st);
 
+// Population evaluation with the angular products on the tensor cores
+// (pop_tc.cu): tiles of kPopTcAtoms atoms of one centre type x
+// kPopTcIndividuals individuals per CTA.  Standard descriptor sizes only
+// (5 x 9 radial and angular, l_max 4, 4-body), at most 3 types, FP32 network.
+constexpr int kPopTcIndividuals = 25;
+constexpr int kPopTcAtoms = 5;
+struct PopTcArgs {
+  int n_tiles, n_mt, n_pop, n_types, n_atoms;
+  const int* tiles;               // [n_tiles][8]: atoms 0..4 (n_atoms = empty), centre type, count
+  const unsigned char* mom_tc;    // per-atom moment blocks (pop_tc_moment_stride bytes each), atom n_atoms = 0
+  size_t mom_tc_stride;
+  const unsigned char* coef_tc;   // [n_types][n_mt] coefficient tiles
+  const float* params;            // [n_pop][lay.words] packed
+  ModelLayout lay;
+  const float* mom; int mom_stride; int v0, w0;   // radial moments (see RadialArgs)
+  float* per_atom; size_t per_atom_stride; int atom_stride;
+  DevStatus* status;
+};
+size_t pop_tc_moment_stride(int rank);
+size_t pop_tc_coef_bytes();
+cudaError_t launch_moments_tc(int n_atoms, int n_types, int rank, const float* amom, int amom_slots,
+                              unsigned char* dst, cudaStream_t st);
+cudaError_t launch_coef_tc(int n_pop, int n_types, int n_mt, const float* params, const ModelLayout& lay,
+                           unsigned char* dst, cudaStream_t st);
+cudaError_t launch_pop_tc(int rank, const PopTcArgs& a, cudaStream_t st);
+
 // Kernel variant keys (must match the compiled instantiations).
 enum Variant { kVarStd = 0, kVarSmall = 1, kVarCount = 2 };
 

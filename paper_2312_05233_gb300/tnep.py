@@ -525,10 +525,10 @@ class Population:
         return rmse, out
 
     def info(self):
-        v = np.zeros(13)
+        v = np.zeros(14)
         _check(_lib.tnep_population_info(self.handle, v.ctypes.data))
         return dict(block=int(v[0]), pop_major=int(v[1]), factored=int(v[2]), tune_ms=v[3:11].tolist(),
-                    last_ms=v[11], atoms=int(v[12]))
+                    last_ms=v[11], atoms=int(v[12]), tensor_core_ms=v[13])
 
     def close(self):
         if self.handle:

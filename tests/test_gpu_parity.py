@@ -591,11 +591,14 @@ def test_population_factored_form(tn, rank, small, n_types):
     params = np.stack([synth.model_params(hp, rng) for _ in range(P)])
     target = rng.standard_normal((bt.n_structs, C))
     preds = {}
-    for form in (1, 2):
+    for form in (1, 2, 3):
         ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc)], n_types, RC)
         tn.tnep_set_option(ctx, tn.TNEP_OPT_POPULATION_FORM, form)
         pop = tn.tnep_population_create(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target)
-        assert pop.info()["factored"] == (1 if form == 2 else 0)
+        if form == 3 and small:  # the tensor-core form takes the standard descriptor only
+            assert pop.info()["factored"] in (0, 1) and pop.info()["tensor_core_ms"] == -1
+        else:
+            assert pop.info()["factored"] == form - 1
         rmse, preds[form] = pop.eval(params, want_out=True)
         np.testing.assert_allclose(rmse, np.sqrt(np.mean((preds[form] - target[None]) ** 2, axis=(1, 2))),
                                    rtol=1e-12)
@@ -607,8 +610,54 @@ def test_population_factored_form(tn, rank, small, n_types):
             a0, a1 = bt.offsets[s_], bt.offsets[s_ + 1]
             r = oracle.evaluate(m, bt.pos[a0:a1], bt.box[s_], bt.types[a0:a1])
             tol = max(REL * np.linalg.norm(r.tensor), COND * np.abs(r.per_atom).sum())
-            for form in (1, 2):
+            for form in (1, 2, 3):
                 assert np.linalg.norm(preds[form][p_, s_] - r.tensor) <= tol, (form, p_, s_)
+
+
+@pytest.mark.parametrize("rank", [1, 2])
+def test_population_tensor_core_form_tiles(tn, rank):
+    """The tensor-core form with 2 individual tiles (P = 31: 25 + 6), three
+    centre types (partial atom tiles of every type), open and periodic
+    structures: every individual and structure against the CUDA-core
+    factored form (same moments, FP32 sums in another order) and sampled
+    individuals against the FP64 oracle."""
+    rng = np.random.default_rng(70 + rank)
+    structs = []
+    for n in (21, 37, 58):
+        p, t, b = synth.anion(n, rng)
+        structs.append(synth.Structure(p.astype(np.float32), (t % 3).astype(np.int32), b.astype(np.float32)))
+    base, types, box = synth.bzo_supercell(3)
+    structs.append(synth.Structure((base + 0.06 * rng.standard_normal(base.shape)).astype(np.float32),
+                                   types.astype(np.int32), box.astype(np.float32)))
+    bt = synth.concat_structures(structs)
+    hp = synth.HyperParams(n_types=3, rank=rank)
+    sc = synth.default_q_scaler(hp)
+    P = 31
+    params = np.stack([synth.model_params(hp, rng) for _ in range(P)])
+    target = rng.standard_normal((bt.n_structs, 3 if rank == 1 else 9))
+    preds = {}
+    for form in (2, 3):
+        ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc)], 3, RC)
+        tn.tnep_set_option(ctx, tn.TNEP_OPT_POPULATION_FORM, form)
+        pop = tn.tnep_population_create(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target)
+        assert pop.info()["factored"] == form - 1
+        for _ in range(2):  # graph replays reuse the operands of the previous generation
+            rmse, preds[form] = pop.eval(params, want_out=True)
+        np.testing.assert_allclose(rmse, np.sqrt(np.mean((preds[form] - target[None]) ** 2, axis=(1, 2))),
+                                   rtol=1e-12)
+        pop.close()
+        ctx.close()
+    for s_ in range(bt.n_structs):
+        a0, a1 = bt.offsets[s_], bt.offsets[s_ + 1]
+        scale = np.linalg.norm(preds[2][:, s_], axis=1).max()
+        for p_ in range(P):
+            d = np.linalg.norm(preds[3][p_, s_] - preds[2][p_, s_])
+            assert d <= REL * scale, (p_, s_, d / scale)
+        for p_ in (0, 24, 25, 30):
+            m = oracle.OracleModel.from_flat(hp, params[p_], sc, *RC)
+            r = oracle.evaluate(m, bt.pos[a0:a1], bt.box[s_], bt.types[a0:a1])
+            tol = max(REL * np.linalg.norm(r.tensor), COND * np.abs(r.per_atom).sum())
+            assert np.linalg.norm(preds[3][p_, s_] - r.tensor) <= tol, (p_, s_)
 
 
 # ------------------------------------------------- tensor-core network
