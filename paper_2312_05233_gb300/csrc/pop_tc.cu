@@ -52,20 +52,38 @@ constexpr int kNT = kPopTcAtoms;        // atoms per CTA
 constexpr int kKW = 96;                 // bf16 per operand row: three terms x K = 32
 constexpr int kGroup = 8 * kKW * 2;     // bytes of 8 rows
 constexpr int kBBytes = 3 * kGroup;     // one atom's B block: 24 rows (lm)
-constexpr int kChunkRows = 72;          // rows of one X product (lm, c)
-constexpr int kChunkBytes = 9 * kGroup;
+// Phase 3 works in rounds of AG atoms (2 for rank 1, 1 for rank 2): one
+// product A over their 24 AG rows of B and one product X over their rows
+// (lm, c) of the Phi / Psi blocks, 72 per atom for rank 1 and 216 for rank
+// 2.  Each N is rounded up to a multiple of 16; the extra rows read whatever
+// follows in shared memory into result columns that are never read.
+template <int RANK> constexpr int x_rows() { return RANK == 1 ? 72 : 216; }
+template <int RANK> constexpr int x_bytes() { return x_rows<RANK>() / 8 * (8 * 96 * 2); }
+template <int RANK> constexpr int round_atoms() { return RANK == 1 ? 2 : 1; }
 constexpr int kCoefBytes = 16 * kGroup;  // 128 rows
+constexpr int kW0Bytes = 30 * 128;      // one individual's W0 (30 rows x 32 floats), staged in phase 2
 constexpr long long kTries = 1LL << 22;
 
 // smem layout (bytes)
 constexpr int kOffC = 0;
 constexpr int kOffB = kOffC + kCoefBytes;              // 16 groups: 5 atoms x 3 + one pad group
-constexpr int kOffX0 = kOffB + 16 * kGroup;            // 10 groups: 72 rows + 8 pad
-constexpr int kOffX1 = kOffX0 + 10 * kGroup;
-constexpr int kOffQ = kOffX1 + 10 * kGroup;            // float [25][5][32] (later the n-sums)
-constexpr int kOffE = kOffQ + kPT * kNT * 32 * 4;      // float [25][5][32]
-constexpr int kOffBar = kOffE + kPT * kNT * 32 * 4;    // 4 mbarriers + TMEM slot
+constexpr int kOffX0 = kOffB + 16 * kGroup;            // the X buffer of one round
+// the n-sums of one round, float [AG][25][5][C], after the X buffer
+template <int RANK> constexpr int off_nsum() { return kOffX0 + round_atoms<RANK>() * x_bytes<RANK>(); }
+template <int RANK> constexpr int nsum_bytes() { return round_atoms<RANK>() * kPT * 5 * (RANK == 1 ? 3 : 9) * 4; }
+// Phase 2 stages the 25 individuals' W0 over [0, kW0Area): individual p at
+// p * kW0Stride (30 rows of 128 B; the stride is 16 B more than the block so
+// that the threads of a warp, which take up to 8 individuals, read rows of
+// different individuals from different banks).  Column 30 of row h holds
+// b0_h and column 31 holds w1_h (the weights there are zero padding).
+constexpr int kW0Stride = kW0Bytes + 16;
+constexpr int kW0Area = ((kPT * kW0Stride + 127) / 128) * 128;
+constexpr int kOffQ = kW0Area;                           // float [25][5][32]: s, then e (slot 30: U)
+constexpr int kOffBar = kOffQ + kPT * kNT * 32 * 4;     // 6 mbarriers + TMEM slot + flag
 constexpr int kSmemBytes = kOffBar + 64;
+static_assert(kW0Area >= off_nsum<1>() + nsum_bytes<1>() && kW0Area >= off_nsum<2>() + nsum_bytes<2>(),
+              "the W0 area covers the operand, X and n-sum buffers");
+static_assert(kOffQ % 16 == 0 && kOffBar % 8 == 0, "alignment");
 
 __device__ __forceinline__ uint32_t tile_off(int row, int part, int k) {
   return tc::kmajor_offset(row, part * 32 + k, kKW);
@@ -155,16 +173,24 @@ __device__ __forceinline__ void issue_split_products(uint32_t d, uint32_t a_base
 template <int RANK>
 __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTcArgs a) {
   constexpr int C = RANK == 1 ? 3 : 9;
-  constexpr int NCH = RANK == 1 ? 1 : 3;  // X products per atom (72 rows each)
+  constexpr int AG = round_atoms<RANK>(), NROUND = (kNT + AG - 1) / AG;
+  constexpr int XR = x_rows<RANK>(), XB = x_bytes<RANK>();
+  constexpr int XN = (AG * XR + 15) / 16 * 16, AN = (AG * 24 + 15) / 16 * 16;
+  constexpr uint32_t TCOLS = 256;
+  static_assert(AN + XN <= (int)TCOLS, "one round fits the TMEM allocation");
   constexpr int NR = 5, NA = 5, BR = 9, NLM = 24, DP = 32;
   extern __shared__ __align__(16) unsigned char smem[];
   float* qbuf = reinterpret_cast<float*>(smem + kOffQ);
-  float* ebuf = reinterpret_cast<float*>(smem + kOffE);
+  float* nsum = reinterpret_cast<float*>(smem + off_nsum<RANK>());
+  // mbarriers: 0 bulk loads, 1 phase-1 product, 2-3 X copies (one per
+  // buffer), 4-5 chunk products (one per TMEM buffer).  Each has at most one
+  // phase outstanding, so its k-th use completes with parity k & 1.
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffBar + 32);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffBar + 48);
   const uint32_t s_base = tc::smem_addr(smem);
   const uint32_t bar_load = tc::smem_addr(&bars[0]), bar_mma = tc::smem_addr(&bars[1]);
   const uint32_t bar_x[2] = {tc::smem_addr(&bars[2]), tc::smem_addr(&bars[3])};
+  const uint32_t bar_c[2] = {tc::smem_addr(&bars[4]), tc::smem_addr(&bars[5])};
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x / a.n_mt, mt = blockIdx.x % a.n_mt;
@@ -176,51 +202,46 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   const int T = a.n_types;
   const size_t xs = a.mom_tc_stride;
   auto atom_of = [&](int i) { return td[i]; };      // a.n_atoms (zero block) for empty slots
-  auto x_src = [&](int q) {
-    const int i = q / NCH, j = q % NCH;
-    return a.mom_tc + (size_t)atom_of(i) * xs + kBBytes + (size_t)j * kChunkBytes;
+  auto x_src = [&](int i) { return a.mom_tc + (size_t)atom_of(i) * xs + kBBytes; };
+  // thread 0: bulk copies of round r's X blocks (the zero block past the tile)
+  auto load_round = [&](int r) {
+    tc::mbar_expect_tx(bar_x[0], AG * XB);
+    for (int ia = 0; ia < AG; ++ia) {
+      const int i = AG * r + ia;
+      tc::bulk_g2s(s_base + kOffX0 + ia * XB, i < kNT ? x_src(i) : a.mom_tc + (size_t)a.n_atoms * xs + kBBytes,
+                   XB, bar_x[0]);
+    }
   };
 
   // ---------------------------------------------------------------- set-up
   if (tid == 0) {
-    for (int b = 0; b < 4; ++b) tc::mbar_init(tc::smem_addr(&bars[b]), 1);
+    for (int b = 0; b < 6; ++b) tc::mbar_init(tc::smem_addr(&bars[b]), 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), 128);
-  // pad groups (never read into a result column, zeroed all the same)
-  for (int k = tid; k < kGroup / 16; k += 128) {
-    const uint4 z = make_uint4(0, 0, 0, 0);
-    reinterpret_cast<uint4*>(smem + kOffB + 15 * kGroup)[k] = z;
-    reinterpret_cast<uint4*>(smem + kOffX0 + 9 * kGroup)[k] = z;
-    reinterpret_cast<uint4*>(smem + kOffX1 + 9 * kGroup)[k] = z;
-  }
-  tc::fence_proxy_async_smem();
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), TCOLS);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
 
-  const int n_chunks = kNT * NCH;
   // issued by thread 0 and not yet observed complete (for the give-up path)
-  int n_commit = 0, x_issued[2] = {0, 0}, x_seen[2] = {0, 0};
-  bool load_seen = false;
-  volatile int* s_flag = reinterpret_cast<volatile int*>(smem + kOffBar + 36);
+  int n_commit = 0, x_issued[2] = {0, 0}, x_seen[2] = {0, 0}, c_issued[2] = {0, 0}, c_seen[2] = {0, 0};
+  int load_issued = 1, load_seen = 0;  // uses of bar_load: phase 1, then phase 3
+  volatile int* s_flag = reinterpret_cast<volatile int*>(smem + kOffBar + 52);
   if (tid == 0) {
     tc::mbar_expect_tx(bar_load, kCoefBytes + kNT * kBBytes);
     tc::bulk_g2s(s_base + kOffC, a.coef_tc + (size_t)(tau * a.n_mt + mt) * kCoefBytes, kCoefBytes, bar_load);
     for (int i = 0; i < kNT; ++i)
       tc::bulk_g2s(s_base + kOffB + i * kBBytes, a.mom_tc + (size_t)atom_of(i) * xs, kBBytes, bar_load);
-    tc::mbar_expect_tx(bar_x[0], kChunkBytes);
-    tc::bulk_g2s(s_base + kOffX0, x_src(0), kChunkBytes, bar_x[0]);
-    x_issued[0] = 1;
   }
 
   // ---------------------------------------------------------------- 1. A for all atoms, q_nl
   bool ok = true;
   int mma_done = 0;  // completions of bar_mma observed by every thread
   if (tid == 0) {
-    ok = load_seen = tc::mbar_wait_bounded(bar_load, 0, kTries);
+    ok = tc::mbar_wait_bounded(bar_load, 0, kTries);
+    if (ok) load_seen = 1;
     if (ok) {
       tc::fence_after_sync();
       issue_split_products(tmem, s_base + kOffC, s_base + kOffB, tc::idesc_bf16_f32(128, 128));
@@ -255,20 +276,17 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
 
   // ---------------------------------------------------------------- 2. network (Eq. 1), radial part
   {
-    float acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.f;
-    float U = 0.f;
+    const ModelLayout& Ly = a.lay;
     const bool mine = prow && x < count;  // thread (p, atom x)
+    // 2a. thread (p, atom x): radial descriptor q_n from the radial moments,
+    // then the scaled descriptor s = q * q_scaler in place
     if (mine) {
-      const int atom = atom_of(x);
-      const ModelLayout& Ly = a.lay;
       const float* model = a.params + (size_t)p * Ly.words;
       const float* cR_i = model + Ly.off_cR + tau * T * Ly.stride_cR;
-      const float* mom = a.mom + atom;
-      float q[DP];
+      const float* mom = a.mom + atom_of(x);
+      float q[NR];
 #pragma unroll
-      for (int d = 0; d < DP; ++d) q[d] = 0.f;
+      for (int n = 0; n < NR; ++n) q[n] = 0.f;
       for (int t = 0; t < T; ++t) {
         float Fk[BR];
 #pragma unroll
@@ -279,46 +297,126 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
 #pragma unroll
           for (int k = 0; k < BR; ++k) q[n] += __ldg(cc + n * BR + k) * Fk[k];
       }
-      const float* qd = qbuf + (pl * kNT + x) * 32;
+      float* qd = qbuf + (pl * kNT + x) * 32;
+      // all scaler loads first (generic stores below would otherwise order them)
+      float scl[DP];
+      const float4* sc4 = reinterpret_cast<const float4*>(model + Ly.off_scaler);
 #pragma unroll
-      for (int d = NR; d < 30; ++d) q[d] = qd[d];
+      for (int v = 0; v < DP / 4; ++v) {
+        const float4 g = __ldg(sc4 + v);
+        scl[4 * v] = g.x; scl[4 * v + 1] = g.y; scl[4 * v + 2] = g.z; scl[4 * v + 3] = g.w;
+      }
+#pragma unroll
+      for (int d = 0; d < 30; ++d) qd[d] = (d < NR ? q[d] : qd[d]) * scl[d];
+      qd[30] = 0.f;
+      qd[31] = 0.f;
+    }
+    // 2b. stage every individual's W0 (cp.async, 16 B per copy) over the
+    // operand buffers, which phase 1 has finished with; then put b0_h, w1_h
+    // into the padding columns 30, 31 of row h.
+    {
       const int net = Ly.nets > 1 ? tau : 0;
-      const float* W0 = model + Ly.off_W0 + net * Ly.H * DP;
-      const float* b0 = model + Ly.off_b0 + net * Ly.H;
-      const float* w1 = model + Ly.off_w1 + net * Ly.H;
-      const float* sc = model + Ly.off_scaler;
-      float s[DP], e[DP];
-#pragma unroll
-      for (int d = 0; d < DP; ++d) {
-        s[d] = d < 30 ? q[d] * __ldg(sc + d) : 0.f;
-        e[d] = 0.f;
-      }
-      U = -__ldg(model + Ly.off_b1 + net);
-      for (int h = 0; h < Ly.H; ++h) {
-        const float4* row = reinterpret_cast<const float4*>(W0 + h * DP);
-        float z = -__ldg(b0 + h);
-#pragma unroll
-        for (int v = 0; v < DP / 4; ++v) {
-          const float4 w = __ldg(row + v);
-          z += w.x * s[4 * v] + w.y * s[4 * v + 1] + w.z * s[4 * v + 2] + w.w * s[4 * v + 3];
-        }
-        const float hh = tanhf(z);
-        const float wh = __ldg(w1 + h);
-        U += wh * hh;
-        const float vh = wh * (1.f - hh * hh);
-#pragma unroll
-        for (int v = 0; v < DP / 4; ++v) {
-          const float4 w = __ldg(row + v);
-          e[4 * v] += vh * w.x; e[4 * v + 1] += vh * w.y; e[4 * v + 2] += vh * w.z; e[4 * v + 3] += vh * w.w;
+      const int H = Ly.H;
+      for (int r = tid; r < kPT * 30 * 8; r += 128) {
+        const int ip = r / 240, h = (r / 8) % 30, c = r % 8;
+        const int pp = mt * kPT + ip;
+        if (pp < a.n_pop && h < H) {
+          const float* src = a.params + (size_t)pp * Ly.words + Ly.off_W0 + (net * H + h) * DP + 4 * c;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + ip * kW0Stride + h * 128 + 16 * c),
+                       "l"(src)
+                       : "memory");
         }
       }
-      float* ed = ebuf + (pl * kNT + x) * 32;
-#pragma unroll
-      for (int d = 0; d < DP; ++d) {
-        e[d] *= d < 30 ? __ldg(sc + d) : 0.f;
-        ed[d] = e[d];
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+      for (int r = tid; r < kPT * 30; r += 128) {
+        const int ip = r / 30, h = r % 30;
+        const int pp = mt * kPT + ip;
+        if (pp < a.n_pop && h < H) {
+          const float* model = a.params + (size_t)pp * Ly.words;
+          float* row = reinterpret_cast<float*>(smem + ip * kW0Stride + h * 128);
+          row[30] = __ldg(model + Ly.off_b0 + net * H + h);
+          row[31] = __ldg(model + Ly.off_w1 + net * H + h);
+        }
       }
-      // radial part of Eqs. 3-4 through the moments V (rank 1) or W (rank 2)
+      __syncthreads();
+      // thread (p, atom x): U = sum_h w1_h tanh(z_h) - b1, z = W0 s - b0,
+      // e = q_scaler * W0^T (w1 * (1 - tanh^2)), written over s in its row
+      if (mine) {
+        const float* model = a.params + (size_t)p * Ly.words;
+        float* row_s = qbuf + (pl * kNT + x) * 32;
+        float sv[DP], e[DP];
+#pragma unroll
+        for (int v = 0; v < DP / 4; ++v) {
+          const float4 t4 = reinterpret_cast<const float4*>(row_s)[v];
+          sv[4 * v] = t4.x; sv[4 * v + 1] = t4.y; sv[4 * v + 2] = t4.z; sv[4 * v + 3] = t4.w;
+        }
+        sv[30] = 0.f;
+        sv[31] = 0.f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) e[d] = 0.f;
+        float U = -__ldg(model + Ly.off_b1 + net);
+        const unsigned char* Wp = smem + pl * kW0Stride;
+        for (int h = 0; h < H; ++h) {
+          const float4* w4 = reinterpret_cast<const float4*>(Wp + h * 128);
+          float w[DP];
+#pragma unroll
+          for (int v = 0; v < DP / 4; ++v) {
+            const float4 t4 = w4[v];
+            w[4 * v] = t4.x; w[4 * v + 1] = t4.y; w[4 * v + 2] = t4.z; w[4 * v + 3] = t4.w;
+          }
+          float zp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int d = 0; d < 30; ++d) zp[d & 3] += w[d] * sv[d];
+          const float z = ((zp[0] + zp[1]) + (zp[2] + zp[3])) - w[30];
+          const float hh = tanhf(z);
+          const float w1h = w[31];
+          U += w1h * hh;
+          const float vh = w1h * (1.f - hh * hh);
+#pragma unroll
+          for (int d = 0; d < 30; ++d) e[d] += vh * w[d];
+        }
+        float scl[DP];
+        const float4* sc4 = reinterpret_cast<const float4*>(model + Ly.off_scaler);
+#pragma unroll
+        for (int v = 0; v < DP / 4; ++v) {
+          const float4 g = __ldg(sc4 + v);
+          scl[4 * v] = g.x; scl[4 * v + 1] = g.y; scl[4 * v + 2] = g.z; scl[4 * v + 3] = g.w;
+        }
+#pragma unroll
+        for (int d = 0; d < 30; ++d) row_s[d] = e[d] * scl[d];
+        row_s[30] = U;
+        row_s[31] = 0.f;
+      }
+    }
+    // the W0 area is refilled by bulk copies (async proxy): order this
+    // phase's generic accesses before them
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    // reload the coefficient tile and the B blocks for phase 3, and the first X chunk
+    if (tid == 0) {
+      tc::mbar_expect_tx(bar_load, kCoefBytes + kNT * kBBytes);
+      tc::bulk_g2s(s_base + kOffC, a.coef_tc + (size_t)(tau * a.n_mt + mt) * kCoefBytes, kCoefBytes, bar_load);
+      for (int i = 0; i < kNT; ++i)
+        tc::bulk_g2s(s_base + kOffB + i * kBBytes, a.mom_tc + (size_t)atom_of(i) * xs, kBBytes, bar_load);
+      load_issued = 2;
+      load_round(0);
+      ++x_issued[0];
+    }
+    // 2c. thread (p, atom x): radial part of Eqs. 3-4 through the moments V
+    // (rank 1) or W (rank 2), and U on the diagonal (rank 2)
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+    if (mine) {
+      const float* model = a.params + (size_t)p * Ly.words;
+      const float* cR_i = model + Ly.off_cR + tau * T * Ly.stride_cR;
+      const float* mom = a.mom + atom_of(x);
+      const float* ed = qbuf + (pl * kNT + x) * 32;
+      float e[NR];
+#pragma unroll
+      for (int n = 0; n < NR; ++n) e[n] = ed[n];
       for (int t = 0; t < T; ++t) {
         const float* cc = cR_i + t * Ly.stride_cR;
 #pragma unroll
@@ -342,46 +440,55 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
           }
         }
       }
-      if constexpr (RANK == 2) { acc[0] += U; acc[4] += U; acc[8] += U; }
+      if constexpr (RANK == 2) {
+        const float U = ed[30];
+        acc[0] += U; acc[4] += U; acc[8] += U;
+      }
     }
-    __syncthreads();  // ebuf complete; qbuf free for the n-sums
 
-    // -------------------------------------------------------------- 3. per atom: A again, X, contraction
-    float G[NLM], part[C];
+    // -------------------------------------------------------------- 3. per round: A again, X, contraction
+    // Round r (atoms AG r ...): the product A (N = AN, TMEM columns [0, AN))
+    // and X (N = XN, columns [AN, AN + XN)).  One X buffer, refilled for
+    // round r + 1 as soon as round r's products have read it (during round
+    // r's epilogue).
+    bool okl = true;
+    if (tid == 0) {
+      okl = tc::mbar_wait_bounded(bar_load, 1, kTries);
+      if (okl) load_seen = 2;
+    }
 #pragma unroll 1
-    for (int i = 0; i < kNT; ++i) {
-#pragma unroll
-      for (int j = 0; j < NCH; ++j) {
-        const int q = i * NCH + j, b = q & 1;
-        bool ok0 = true;
-        if (tid == 0) {
-          ok0 = tc::mbar_wait_bounded(bar_x[b], (q >> 1) & 1, kTries);
-          if (ok0) {
-            ++x_seen[b];
-            // the other buffer's last product has completed: refill it
-            if (q + 1 < n_chunks) {
-              tc::mbar_expect_tx(bar_x[b ^ 1], kChunkBytes);
-              tc::bulk_g2s(s_base + (b ? kOffX0 : kOffX1), x_src(q + 1), kChunkBytes, bar_x[b ^ 1]);
-              ++x_issued[b ^ 1];
-            }
-            tc::fence_after_sync();
-            if (j == 0)
-              issue_split_products(tmem, s_base + kOffC, s_base + kOffB + 3 * i * kGroup,
-                                   tc::idesc_bf16_f32(128, 32));
-            issue_split_products(tmem + 32, s_base + kOffC, s_base + (b ? kOffX1 : kOffX0),
-                                 tc::idesc_bf16_f32(128, 80));
-            tc::commit_to(bar_mma);
-            ++n_commit;
-          }
+    for (int r = 0; r < NROUND; ++r) {
+      bool ok0 = okl;
+      if (tid == 0 && ok0) {
+        ok0 = tc::mbar_wait_bounded(bar_x[0], r & 1, kTries);
+        if (ok0) {
+          ++x_seen[0];
+          tc::fence_after_sync();
+          issue_split_products(tmem, s_base + kOffC, s_base + kOffB + 3 * AG * r * kGroup, tc::idesc_bf16_f32(128, AN));
+          issue_split_products(tmem + AN, s_base + kOffC, s_base + kOffX0, tc::idesc_bf16_f32(128, XN));
+          tc::commit_to(bar_c[0]);
+          ++c_issued[0];
         }
-        ok = __syncthreads_and(ok0 && tc::mbar_wait_bounded(bar_mma, mma_done & 1, kTries)) != 0;
-        if (!ok) goto give_up;
-        ++mma_done;
-        tc::fence_after_sync();
-        if (j == 0) {
+      }
+      ok = __syncthreads_and(ok0 && tc::mbar_wait_bounded(bar_c[0], r & 1, kTries)) != 0;
+      if (!ok) goto give_up;
+      if (tid == 0) {
+        ++c_seen[0];
+        if (r + 1 < NROUND) {  // round r's products have read the buffer
+          load_round(r + 1);
+          ++x_issued[0];
+        }
+      }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int ia = 0; ia < AG; ++ia) {
+        const int i = AG * r + ia;
+        if (i >= kNT) break;
+        float G[NLM], part[C];
+        {
           float Av[32];
-          tc::tmem_ld32(lane_base, Av);
-          const float* ed = ebuf + (pl * kNT + i) * 32;
+          tc::tmem_ld32(lane_base + 24 * ia, Av);
+          const float* ed = qbuf + (pl * kNT + i) * 32;
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm)
             G[lm] = prow ? 2.f * wlm(lm) * ed[NR + (l_of(lm) - 1) * NA + x] * Av[lm] : 0.f;
@@ -395,25 +502,30 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
 #pragma unroll
           for (int c = 0; c < C; ++c) part[c] = 0.f;
         }
-        // X column 32 + f, f = lm' * C + c with lm = (72 / C) j + lm'
+        // X column AN + XR ia + f, f = lm * C + c
 #pragma unroll
-        for (int blk = 0; blk < 3; ++blk) {
+        for (int blk = 0; blk < (XR + 31) / 32; ++blk) {
           float Xv[32];
-          tc::tmem_ld32(lane_base + 32 + 32 * blk, Xv);
+          tc::tmem_ld32(lane_base + AN + XR * ia + 32 * blk, Xv);
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            const int f = 32 * blk + u;
-            if (f < kChunkRows) part[f % C] += G[(kChunkRows / C) * j + f / C] * Xv[u];
+          for (int v = 0; v < 32; ++v) {
+            const int f = 32 * blk + v;
+            if (f < XR) part[f % C] += G[f / C] * Xv[v];
           }
         }
-        float* red = qbuf + (i & 1) * (kPT * 5 * C);
-        if (j == NCH - 1 && prow) {
+        float* red = nsum + ia * (kPT * 5 * C);
+        if (prow) {
 #pragma unroll
           for (int c = 0; c < C; ++c) red[(pl * 5 + x) * C + c] = part[c];
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        if (j == NCH - 1 && mine && x == i) {
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+#pragma unroll
+      for (int ia = 0; ia < AG; ++ia) {
+        const int i = AG * r + ia;
+        if (i < kNT && mine && x == i) {
+          const float* red = nsum + ia * (kPT * 5 * C);
           float* out = a.per_atom + (size_t)p * a.per_atom_stride + atom_of(i);
 #pragma unroll
           for (int c = 0; c < C; ++c) {
@@ -424,9 +536,10 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
           }
         }
       }
+      __syncthreads();  // the n-sums are read before the next round rewrites them
     }
   }
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
   return;
 
 give_up:
@@ -437,10 +550,12 @@ give_up:
   if (tid == 0) {
     if (a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
     bool drained = true;
-    if (!load_seen) drained = tc::mbar_wait_bounded(bar_load, 0, kTries) && drained;
-    if (n_commit > mma_done) drained = tc::mbar_wait_bounded(bar_mma, (n_commit - 1) & 1, kTries) && drained;
-    for (int b = 0; b < 2; ++b)
+    if (load_issued > load_seen) drained = tc::mbar_wait_bounded(bar_load, (load_issued - 1) & 1, kTries) && drained;
+    if (n_commit > mma_done) drained = tc::mbar_wait_bounded(bar_mma, 0, kTries) && drained;
+    for (int b = 0; b < 2; ++b) {
       if (x_issued[b] > x_seen[b]) drained = tc::mbar_wait_bounded(bar_x[b], (x_issued[b] - 1) & 1, kTries) && drained;
+      if (c_issued[b] > c_seen[b]) drained = tc::mbar_wait_bounded(bar_c[b], (c_issued[b] - 1) & 1, kTries) && drained;
+    }
     *s_flag = drained ? 1 : 0;
   }
   __syncthreads();
@@ -448,13 +563,13 @@ give_up:
     tc::fence_after_sync();
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
   }
 }
 
 }  // namespace
 
-size_t pop_tc_moment_stride(int rank) { return (size_t)kBBytes + (size_t)(rank == 1 ? 1 : 3) * kChunkBytes; }
+size_t pop_tc_moment_stride(int rank) { return (size_t)kBBytes + (size_t)(rank == 1 ? x_bytes<1>() : x_bytes<2>()); }
 size_t pop_tc_coef_bytes() { return kCoefBytes; }
 
 cudaError_t launch_moments_tc(int n_atoms, int n_types, int rank, const float* amom, int amom_slots,
