@@ -330,14 +330,25 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
       asm volatile("cp.async.commit_group;" ::: "memory");
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncthreads();
-      for (int r = tid; r < kPT * 30; r += 128) {
-        const int ip = r / 30, h = r % 30;
-        const int pp = mt * kPT + ip;
-        if (pp < a.n_pop && h < H) {
-          const float* model = a.params + (size_t)pp * Ly.words;
-          float* row = reinterpret_cast<float*>(smem + ip * kW0Stride + h * 128);
-          row[30] = __ldg(model + Ly.off_b0 + net * H + h);
-          row[31] = __ldg(model + Ly.off_w1 + net * H + h);
+      {
+        constexpr int NPR = (kPT * 30 + 127) / 128;  // rows patched per thread
+        float pb0[NPR], pw1[NPR];
+#pragma unroll
+        for (int u = 0; u < NPR; ++u) {  // all loads first, then the stores
+          const int r = tid + 128 * u, ip = r / 30, h = r % 30, pp = mt * kPT + ip;
+          const bool v = r < kPT * 30 && pp < a.n_pop && h < H;
+          const float* model = a.params + (size_t)(v ? pp : 0) * Ly.words;
+          pb0[u] = v ? __ldg(model + Ly.off_b0 + net * H + h) : 0.f;
+          pw1[u] = v ? __ldg(model + Ly.off_w1 + net * H + h) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < NPR; ++u) {
+          const int r = tid + 128 * u, ip = r / 30, h = r % 30;
+          if (r < kPT * 30) {
+            float* row = reinterpret_cast<float*>(smem + ip * kW0Stride + h * 128);
+            row[30] = pb0[u];
+            row[31] = pw1[u];
+          }
         }
       }
       __syncthreads();
@@ -358,6 +369,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
         for (int d = 0; d < DP; ++d) e[d] = 0.f;
         float U = -__ldg(model + Ly.off_b1 + net);
         const unsigned char* Wp = smem + pl * kW0Stride;
+#pragma unroll 2
         for (int h = 0; h < H; ++h) {
           const float4* w4 = reinterpret_cast<const float4*>(Wp + h * 128);
           float w[DP];
