@@ -336,17 +336,19 @@ def serving_bench(tn, synth, device, rates, n_req):
             "mean_atoms": float(atoms.mean()), "rates": out}
 
 
-def population_bench(tn, synth, device, n_pop=50, gens=5):
+def population_bench(tn, synth, device, n_pop=50, gens=5, rank=1):
     """50 parameter vectors x 600 uneven structures per generation (open water
-    clusters of 3-300 atoms, periodic boxes of 192-1,536 atoms), dipole RMSE
-    against seeded random targets; structures resident, generations replayed
-    from a CUDA graph with the autotuned launch shape."""
-    rng = np.random.default_rng(synth.seed_for(4, 9))
+    clusters of 3-300 atoms, periodic boxes of 192-1,536 atoms), RMSE of the
+    dipole (rank 1) or polarizability (rank 2) against seeded random targets;
+    structures resident, generations replayed from a CUDA graph with the
+    autotuned form and launch shape (per-pair walk, factored on the CUDA
+    cores, factored with tensor-core products)."""
+    rng = np.random.default_rng(synth.seed_for(4, 9 + 10 * (rank - 1)))
     structs = synth.population_structures()
     bt = synth.concat_structures(structs)
-    hp = synth.HyperParams(n_types=2, rank=1)
+    hp = synth.HyperParams(n_types=2, rank=rank)
     sc = synth.default_q_scaler(hp)
-    target = rng.standard_normal((bt.n_structs, 3))
+    target = rng.standard_normal((bt.n_structs, 3 if rank == 1 else 9))
     gen_params = [np.stack([synth.model_params(hp, rng) for _ in range(n_pop)]) for _ in range(gens + 1)]
     ctx = tn.tnep_create([tn.Model.from_hyper(hp, gen_params[0][0], sc)], 2, RC, device=device)
     pop = tn.tnep_population_create(ctx, 0, gen_params[0], bt.offsets, bt.pos, bt.box, bt.types, target)
@@ -364,12 +366,14 @@ def population_bench(tn, synth, device, n_pop=50, gens=5):
     pop.close()
     ctx.close()
     atoms = len(bt.types)
-    return {"workload": f"{n_pop} parameter vectors x {bt.n_structs} structures ({atoms} atoms), rank 1",
+    forms = {0: "per-pair walk", 1: "factored, CUDA cores", 2: "factored, tensor-core products"}
+    return {"workload": f"{n_pop} parameter vectors x {bt.n_structs} structures ({atoms} atoms), rank {rank}",
             "generation_ms": wall * 1e3, "generation_device_ms": dev_ms / gens,
             "atom_evals_per_s": n_pop * atoms / wall, "oneshot_ms": oneshot * 1e3,
             "chosen": {"atoms_per_cta": info["block"], "individual_major": info["pop_major"],
-                       "factored": info["factored"]},
-            "candidates_ms": info["tune_ms"], "rmse_first": float(rmse[0])}
+                       "factored": info["factored"], "form": forms[info["factored"]]},
+            "candidates_ms": info["tune_ms"], "tensor_core_form_ms": info["tensor_core_ms"],
+            "rmse_first": float(rmse[0])}
 
 
 def snes_bench(tn, synth, device, n_pop=50, gens=100):
@@ -797,6 +801,7 @@ def main():
             line["precision"] = precision_report(tn, synth, local, pool)
     if rank == 0 and not args.no_population:
         line["population"] = population_bench(tn, synth, local)
+        line["population_rank2"] = population_bench(tn, synth, local, rank=2)
     if rank == 0 and not args.no_population:
         line["snes"] = snes_bench(tn, synth, local)
     if rank == 0 and not args.no_population:
