@@ -78,8 +78,11 @@ template <int RANK> constexpr int nsum_bytes() { return round_atoms<RANK>() * kP
 // b0_h and column 31 holds w1_h (the weights there are zero padding).
 constexpr int kW0Stride = kW0Bytes + 16;
 constexpr int kW0Area = ((kPT * kW0Stride + 127) / 128) * 128;
-constexpr int kOffQ = kW0Area;                           // float [25][5][32]: s, then e (slot 30: U)
-constexpr int kOffBar = kOffQ + kPT * kNT * 32 * 4;     // 6 mbarriers + TMEM slot + flag
+// rows of 36 floats (s, then e; slot 30: U): a stride of 144 B puts the rows
+// read by eight consecutive threads in different banks
+constexpr int kQS = 36;
+constexpr int kOffQ = kW0Area;                           // float [25][5][kQS]
+constexpr int kOffBar = kOffQ + kPT * kNT * kQS * 4;    // 6 mbarriers + TMEM slot + flag
 constexpr int kSmemBytes = kOffBar + 64;
 static_assert(kW0Area >= off_nsum<1>() + nsum_bytes<1>() && kW0Area >= off_nsum<2>() + nsum_bytes<2>(),
               "the W0 area covers the operand, X and n-sum buffers");
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
     float A[32];
     tc::tmem_ld32(lane_base + i * 24, A);
     if (prow) {
-      float* qd = qbuf + (pl * kNT + i) * 32;
+      float* qd = qbuf + (pl * kNT + i) * kQS;
 #pragma unroll
       for (int l = 1; l <= 4; ++l) {
         float s = 0.f;
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
 #pragma unroll
           for (int k = 0; k < BR; ++k) q[n] += __ldg(cc + n * BR + k) * Fk[k];
       }
-      float* qd = qbuf + (pl * kNT + x) * 32;
+      float* qd = qbuf + (pl * kNT + x) * kQS;
       // all scaler loads first (generic stores below would otherwise order them)
       float scl[DP];
       const float4* sc4 = reinterpret_cast<const float4*>(model + Ly.off_scaler);
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
       // e = q_scaler * W0^T (w1 * (1 - tanh^2)), written over s in its row
       if (mine) {
         const float* model = a.params + (size_t)p * Ly.words;
-        float* row_s = qbuf + (pl * kNT + x) * 32;
+        float* row_s = qbuf + (pl * kNT + x) * kQS;
         float sv[DP], e[DP];
 #pragma unroll
         for (int v = 0; v < DP / 4; ++v) {
@@ -396,10 +399,15 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
           const float4 g = __ldg(sc4 + v);
           scl[4 * v] = g.x; scl[4 * v + 1] = g.y; scl[4 * v + 2] = g.z; scl[4 * v + 3] = g.w;
         }
+        e[30] = U;
+        e[31] = 0.f;
+        scl[30] = 1.f;
+        scl[31] = 1.f;
 #pragma unroll
-        for (int d = 0; d < 30; ++d) row_s[d] = e[d] * scl[d];
-        row_s[30] = U;
-        row_s[31] = 0.f;
+        for (int v = 0; v < DP / 4; ++v)
+          reinterpret_cast<float4*>(row_s)[v] =
+              make_float4(e[4 * v] * scl[4 * v], e[4 * v + 1] * scl[4 * v + 1], e[4 * v + 2] * scl[4 * v + 2],
+                          e[4 * v + 3] * scl[4 * v + 3]);
       }
     }
     // the W0 area is refilled by bulk copies (async proxy): order this
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
       const float* model = a.params + (size_t)p * Ly.words;
       const float* cR_i = model + Ly.off_cR + tau * T * Ly.stride_cR;
       const float* mom = a.mom + atom_of(x);
-      const float* ed = qbuf + (pl * kNT + x) * 32;
+      const float* ed = qbuf + (pl * kNT + x) * kQS;
       float e[NR];
 #pragma unroll
       for (int n = 0; n < NR; ++n) e[n] = ed[n];
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
         {
           float Av[32];
           tc::tmem_ld32(lane_base + 24 * ia, Av);
-          const float* ed = qbuf + (pl * kNT + i) * 32;
+          const float* ed = qbuf + (pl * kNT + i) * kQS;
 #pragma unroll
           for (int lm = 0; lm < NLM; ++lm)
             G[lm] = prow ? 2.f * wlm(lm) * ed[NR + (l_of(lm) - 1) * NA + x] * Av[lm] : 0.f;
