@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   const uint32_t bar_load = tc::smem_addr(&bars[0]), bar_mma = tc::smem_addr(&bars[1]);
   const uint32_t bar_x[2] = {tc::smem_addr(&bars[2]), tc::smem_addr(&bars[3])};
   const uint32_t bar_c[2] = {tc::smem_addr(&bars[4]), tc::smem_addr(&bars[5])};
+  const uint32_t bar_w = bar_c[1];  // the weight blocks of phase 2 (the second product barrier is unused)
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x / a.n_mt, mt = blockIdx.x % a.n_mt;
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   // issued by thread 0 and not yet observed complete (for the give-up path)
   int n_commit = 0, x_issued[2] = {0, 0}, x_seen[2] = {0, 0}, c_issued[2] = {0, 0}, c_seen[2] = {0, 0};
   int load_issued = 1, load_seen = 0;  // uses of bar_load: phase 1, then phase 3
+  bool w_issued = false, w_seen = false;
   volatile int* s_flag = reinterpret_cast<volatile int*>(smem + kOffBar + 52);
   if (tid == 0) {
     tc::mbar_expect_tx(bar_load, kCoefBytes + kNT * kBBytes);
@@ -255,6 +257,19 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   ok = __syncthreads_and(ok && tc::mbar_wait_bounded(bar_mma, 0, kTries)) != 0;
   if (!ok) goto give_up;
   mma_done = 1;
+  // the product has read the operand buffers: stage every individual's W0
+  // block over them now (one bulk copy each), to land during q and 2a
+  if (tid == 0) {
+    const int net = a.lay.nets > 1 ? tau : 0;
+    int nw = 0;
+    for (int ip = 0; ip < kPT; ++ip) nw += (mt * kPT + ip < a.n_pop) ? 1 : 0;
+    tc::mbar_expect_tx(bar_w, nw * kW0Bytes);
+    for (int ip = 0; ip < nw; ++ip)
+      tc::bulk_g2s(s_base + ip * kW0Stride,
+                   a.params + (size_t)(mt * kPT + ip) * a.lay.words + a.lay.off_W0 + net * a.lay.H * DP, kW0Bytes,
+                   bar_w);
+    w_issued = true;
+  }
   tc::fence_after_sync();
 #pragma unroll 1
   for (int i = 0; i < kNT; ++i) {
@@ -309,49 +324,45 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
         const float4 g = __ldg(sc4 + v);
         scl[4 * v] = g.x; scl[4 * v + 1] = g.y; scl[4 * v + 2] = g.z; scl[4 * v + 3] = g.w;
       }
+      float4* q4 = reinterpret_cast<float4*>(qd);
 #pragma unroll
-      for (int d = 0; d < 30; ++d) qd[d] = (d < NR ? q[d] : qd[d]) * scl[d];
-      qd[30] = 0.f;
-      qd[31] = 0.f;
+      for (int v = 0; v < DP / 4; ++v) {
+        float4 t4 = q4[v];
+        float r4[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int d = 4 * v + u;
+          r4[u] = d < NR ? q[d < NR ? d : 0] * scl[d] : (d < 30 ? r4[u] * scl[d] : 0.f);
+        }
+        q4[v] = make_float4(r4[0], r4[1], r4[2], r4[3]);
+      }
     }
-    // 2b. stage every individual's W0 (cp.async, 16 B per copy) over the
-    // operand buffers, which phase 1 has finished with; then put b0_h, w1_h
-    // into the padding columns 30, 31 of row h.
+    // 2b. every individual's W0 block has been staged by bulk copies (issued
+    // after the first product); b0_h and w1_h go into its padding columns 30,
+    // 31 of row h.
     {
       const int net = Ly.nets > 1 ? tau : 0;
       const int H = Ly.H;
-      for (int r = tid; r < kPT * 30 * 8; r += 128) {
-        const int ip = r / 240, h = (r / 8) % 30, c = r % 8;
-        const int pp = mt * kPT + ip;
-        if (pp < a.n_pop && h < H) {
-          const float* src = a.params + (size_t)pp * Ly.words + Ly.off_W0 + (net * H + h) * DP + 4 * c;
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + ip * kW0Stride + h * 128 + 16 * c),
-                       "l"(src)
-                       : "memory");
-        }
+      constexpr int NPR = (kPT * 30 + 127) / 128;  // rows patched per thread
+      float pb0[NPR], pw1[NPR];
+#pragma unroll
+      for (int u = 0; u < NPR; ++u) {
+        const int r = tid + 128 * u, ip = r / 30, h = r % 30, pp = mt * kPT + ip;
+        const bool v = r < kPT * 30 && pp < a.n_pop && h < H;
+        const float* model = a.params + (size_t)(v ? pp : 0) * Ly.words;
+        pb0[u] = v ? __ldg(model + Ly.off_b0 + net * H + h) : 0.f;
+        pw1[u] = v ? __ldg(model + Ly.off_w1 + net * H + h) : 0.f;
       }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncthreads();
-      {
-        constexpr int NPR = (kPT * 30 + 127) / 128;  // rows patched per thread
-        float pb0[NPR], pw1[NPR];
+      const bool okw = __syncthreads_and(tc::mbar_wait_bounded(bar_w, 0, kTries)) != 0;
+      if (!okw) goto give_up;
+      if (tid == 0) w_seen = true;
 #pragma unroll
-        for (int u = 0; u < NPR; ++u) {  // all loads first, then the stores
-          const int r = tid + 128 * u, ip = r / 30, h = r % 30, pp = mt * kPT + ip;
-          const bool v = r < kPT * 30 && pp < a.n_pop && h < H;
-          const float* model = a.params + (size_t)(v ? pp : 0) * Ly.words;
-          pb0[u] = v ? __ldg(model + Ly.off_b0 + net * H + h) : 0.f;
-          pw1[u] = v ? __ldg(model + Ly.off_w1 + net * H + h) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < NPR; ++u) {
-          const int r = tid + 128 * u, ip = r / 30, h = r % 30;
-          if (r < kPT * 30) {
-            float* row = reinterpret_cast<float*>(smem + ip * kW0Stride + h * 128);
-            row[30] = pb0[u];
-            row[31] = pw1[u];
-          }
+      for (int u = 0; u < NPR; ++u) {
+        const int r = tid + 128 * u, ip = r / 30, h = r % 30;
+        if (r < kPT * 30) {
+          float* row = reinterpret_cast<float*>(smem + ip * kW0Stride + h * 128);
+          row[30] = pb0[u];
+          row[31] = pw1[u];
         }
       }
       __syncthreads();
@@ -572,10 +583,10 @@ give_up:
     bool drained = true;
     if (load_issued > load_seen) drained = tc::mbar_wait_bounded(bar_load, (load_issued - 1) & 1, kTries) && drained;
     if (n_commit > mma_done) drained = tc::mbar_wait_bounded(bar_mma, 0, kTries) && drained;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 2; ++b)
       if (x_issued[b] > x_seen[b]) drained = tc::mbar_wait_bounded(bar_x[b], (x_issued[b] - 1) & 1, kTries) && drained;
-      if (c_issued[b] > c_seen[b]) drained = tc::mbar_wait_bounded(bar_c[b], (c_issued[b] - 1) & 1, kTries) && drained;
-    }
+    if (c_issued[0] > c_seen[0]) drained = tc::mbar_wait_bounded(bar_c[0], (c_issued[0] - 1) & 1, kTries) && drained;
+    if (w_issued && !w_seen) drained = tc::mbar_wait_bounded(bar_w, 0, kTries) && drained;
     *s_flag = drained ? 1 : 0;
   }
   __syncthreads();
