@@ -258,17 +258,21 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   if (!ok) goto give_up;
   mma_done = 1;
   // the product has read the operand buffers: stage every individual's W0
-  // block over them now (one bulk copy each), to land during q and 2a
-  if (tid == 0) {
-    const int net = a.lay.nets > 1 ? tau : 0;
-    int nw = 0;
-    for (int ip = 0; ip < kPT; ++ip) nw += (mt * kPT + ip < a.n_pop) ? 1 : 0;
-    tc::mbar_expect_tx(bar_w, nw * kW0Bytes);
-    for (int ip = 0; ip < nw; ++ip)
-      tc::bulk_g2s(s_base + ip * kW0Stride,
-                   a.params + (size_t)(mt * kPT + ip) * a.lay.words + a.lay.off_W0 + net * a.lay.H * DP, kW0Bytes,
+  // block over them now (one bulk copy each, issued by thread ip), to land
+  // during q and 2a.  Thread 0 arms the byte count; a copy that completes
+  // first cannot end the phase, which also waits for that arrival.
+  {
+    const int nw = min(kPT, a.n_pop - mt * kPT);
+    if (tid == 0) {
+      tc::mbar_expect_tx(bar_w, nw * kW0Bytes);
+      w_issued = true;
+    }
+    if (tid < nw) {
+      const int net = a.lay.nets > 1 ? tau : 0;
+      tc::bulk_g2s(s_base + tid * kW0Stride,
+                   a.params + (size_t)(mt * kPT + tid) * a.lay.words + a.lay.off_W0 + net * a.lay.H * DP, kW0Bytes,
                    bar_w);
-    w_issued = true;
+    }
   }
   tc::fence_after_sync();
 #pragma unroll 1
