@@ -443,11 +443,16 @@ enum {
                                        rc_R / k_x along x; for k_x > 1 each atom scans, in each (y, z) row of its
                                        stencil, only the x-cells that meet [x_i - h, x_i + h], h^2 = rc_R^2 -
                                        (distance from atom i to the row)^2.  Same pair sets; list order may differ. */
-  TNEP_OPT_ALLOC_COUNT = 12         /* read-only: device and pinned-host allocations made by the library in this
+  TNEP_OPT_ALLOC_COUNT = 12,        /* read-only: device and pinned-host allocations made by the library in this
                                        process so far.  Host-side fault injection: with the environment variable
                                        TNEP_FAULT=oom@N set before the library is loaded, allocation number N
                                        fails once (nothing is allocated, the device is untouched) and the call
                                        making it returns TNEP_ERR_OOM; the context stays usable. */
+  TNEP_OPT_WAIT_TRIES = 13          /* try_wait limit of the device-side waits for the tensor-core network's
+                                       products (default 4194304).  A CTA whose wait runs out stores nothing,
+                                       waits (with the default limit) for its product to finish, frees its tensor
+                                       memory and makes the call return TNEP_ERR_TIMEOUT; 0 makes every such
+                                       wait give up at once (used to test that path).  The context stays usable. */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

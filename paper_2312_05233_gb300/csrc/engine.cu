@@ -354,6 +354,7 @@ FusedArgs fused_args(tnep_ctx* c, Workspace& w, const Model& m, int N) {
   f.rc_R = c->rc_R;
   f.rc_A = c->rc_A;
   f.atom_stride = w.atom_stride;
+  f.wait_tries = c->wait_tries;
   return f;
 }
 
@@ -425,6 +426,8 @@ tnep_status check_status(tnep_ctx* c, const DevStatus& s, bool* regrow) {
   *regrow = false;
   if (s.error == TNEP_ERR_BOX_TOO_SMALL)
     return fail(TNEP_ERR_BOX_TOO_SMALL, "structure " + std::to_string(s.bad_struct) + ": periodic edge < 2 rc_R");
+  if (s.error == TNEP_ERR_TIMEOUT)
+    return fail(TNEP_ERR_TIMEOUT, "a device-side bounded wait gave up (tensor-core product not completed in time)");
   if (s.error) return fail((tnep_status)s.error, "invalid input in structure " + std::to_string(s.bad_struct));
   if (s.max_cnt_R > c->cap_R || s.max_cnt_A > c->cap_A) {
     const int need_R = std::max(c->cap_R, round_up(s.max_cnt_R + 8, 32));

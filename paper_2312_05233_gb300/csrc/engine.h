@@ -166,7 +166,8 @@ struct tnep_ctx {
   Workspace skin_ws;       // skin lists of the current pass's first frame
   int last_skin_used = 0;  // the last tnep_eval reused skin lists in every pass
   int block_atoms = 128;  // atoms per CTA of the fused kernel (64 or 128)
-  int population_form = 0;  // 0 = timed choice, 1 = per-pair walk, 2 = factored
+  int population_form = 0;  // 0 = timed choice, 1 = per-pair walk, 2 = factored, 3 = factored on the tensor cores
+  long long wait_tries = tnep::kDefaultWaitTries;  // bounded-wait limit of the tensor-core network
   double last_kernel_ms = 0.0;
   double last_nbr_ms = 0.0;
   int last_launches = 0;

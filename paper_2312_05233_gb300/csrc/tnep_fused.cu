@@ -101,7 +101,7 @@ __host__ __device__ constexpr int tc_smem_bytes(int nets) { return 128 + 128 * 6
 __host__ __device__ constexpr uint32_t tc_tmem_cols(int nets) {
   return nets * 32 <= 32 ? 32u : nets * 32 <= 64 ? 64u : nets * 32 <= 128 ? 128u : 256u;
 }
-constexpr long long kMbarTries = 1LL << 22;
+constexpr long long kMbarTries = kDefaultWaitTries;
 
 // TCM: 0 = FP32 network on the CUDA cores; 1 = network products on the
 // tensor cores with BF16 operands and FP32 accumulation; 2 = the same with
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       }
       // every thread polls the mbarrier itself; the barrier-and makes the
       // give-up decision the same for the whole CTA
-      const bool ok = __syncthreads_and(tc::mbar_wait_bounded(mbar, parity, kMbarTries)) != 0;
+      const bool ok = __syncthreads_and(tc::mbar_wait_bounded(mbar, parity, a.wait_tries)) != 0;
       tc::fence_after_sync();
       return ok;
     };
@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     // -- and returns without storing a result.  If the completion never
     // arrives, the CTA exits with its columns still allocated rather than
     // free columns a product may still write; the host gets TNEP_ERR_TIMEOUT.
+    // The product waits use the context's limit (TNEP_OPT_WAIT_TRIES); the
+    // drain always uses the default one, so that a small limit only makes
+    // the call give up, never leaves TMEM allocated.
     uint32_t pending = 0;  // parity of the product whose completion is awaited
     bool ok = gemm(tileB1, 0);
     float z[32];

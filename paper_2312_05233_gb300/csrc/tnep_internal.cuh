@@ -169,7 +169,10 @@ struct FusedArgs {
   int pop_major;             // 1: blockIdx.x = individual, blockIdx.y = atom block
   const float* amom; int amom_slots;   // angular moments (factored population path), else null
   DevStatus* status;         // error word (bounded waits of the tensor-core path)
+  long long wait_tries;      // try_wait limit of the tensor-core network's product waits
 };
+// Default try_wait limit of the device-side bounded waits.
+constexpr long long kDefaultWaitTries = 1LL << 22;
 
 // Angular moments of the basis for population evaluation (angmom.cu): B, and
 // Phi (rank 1) or Psi (rank 2).  Per (t, k) the B block holds NLM slots padded

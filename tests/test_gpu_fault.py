@@ -58,3 +58,33 @@ def test_allocation_failures_return_oom_and_leave_the_context_usable(built):
         np.testing.assert_allclose(p, pr, rtol=0, atol=1e-6 * np.abs(pr).max())
     # every kind of call met an allocation failure in some run
     assert {"create", "eval", "submit", "population_create"} <= hit, hit
+
+
+def test_tensor_core_wait_give_up_reports_timeout_and_context_recovers(built):
+    """Device-side bounded waits: with TNEP_OPT_WAIT_TRIES = 0 every wait of
+    the tensor-core network for its product gives up at once.  Each CTA then
+    stores nothing, waits (with the default limit) for the product it issued,
+    frees its tensor memory and raises TNEP_ERR_TIMEOUT, which the call
+    returns.  No wait is left unbounded and nothing faults; afterwards the
+    same context gives the results of a fault-free call bit for bit."""
+    import synth
+    from paper_2312_05233_gb300 import tnep as tn
+    frames, types, box = synth.water_small(3)
+    rng = np.random.default_rng(5)
+    models = []
+    for rank in (1, 2):
+        hp = synth.HyperParams(n_types=2, rank=rank)
+        models.append(tn.Model.from_hyper(hp, synth.model_params(hp, rng), synth.default_q_scaler(hp),
+                                          mlp_precision=2))
+    ctx = tn.tnep_create(models, 2, (6.0, 4.0))
+    ref = tn.tnep_eval(ctx, frames, box, types)
+    default = tn.tnep_get_option(ctx, tn.TNEP_OPT_WAIT_TRIES)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_WAIT_TRIES, 0)
+    with pytest.raises(tn.TnepError) as e:
+        tn.tnep_eval(ctx, frames, box, types)
+    assert e.value.status == tn.TNEP_ERR_TIMEOUT and "bounded wait" in str(e.value)
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_WAIT_TRIES, default)
+    again = tn.tnep_eval(ctx, frames, box, types)
+    for a, b in zip(ref, again):
+        assert np.array_equal(a, b)
+    ctx.close()
