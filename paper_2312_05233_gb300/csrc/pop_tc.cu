@@ -21,16 +21,21 @@
 // One CTA (128 threads) takes one tile of 5 atoms of one centre type and 25
 // individuals.  TMEM lane r = 5 p + n holds row (p, n).
 //   1. bulk copies (cp.async.bulk, mbarrier) of the coefficient tile and of
-//      the 5 atoms' B blocks into shared memory; one product A for all 5
-//      atoms (N = 128 columns); lane (p, n) reads its A_{n,lm}(i) and forms
-//      q_nl and the 4-body term of its n for each atom.
-//   2. thread (p, i): radial descriptor from the radial moments, the FP32
-//      network (Eq. 1), dU/dq and the radial part of Eqs. 3-4.
-//   3. per atom (and, for rank 2, per third of its lm): the product A again
-//      (N = 32) and X (N = 80) from a double-buffered bulk copy of the Phi
-//      block; lane (p, n) forms G_{n,lm} and its partial contraction; thread
+//      the 5 atoms' B blocks; one product A for all 5 atoms (N = 128
+//      columns); lane (p, n) reads its A_{n,lm}(i) and forms q_nl and the
+//      4-body term of its n for each atom.  As soon as the product has read
+//      its operands, the 25 individuals' W0 blocks are bulk-copied over them.
+//   2. thread (p, i): radial descriptor from the radial moments; the FP32
+//      network (Eq. 1) on the staged weights (b0, w1 in the rows' padding
+//      columns), dU/dq written over the descriptor row; the radial part of
+//      Eqs. 3-4.  Meanwhile the coefficient tile and the B blocks are loaded
+//      again, with the first round's Phi / Psi blocks.
+//   3. rounds of AG atoms (2 for rank 1, 1 for rank 2): the product A again
+//      (N = 32 or 48) and X over the round's Phi / Psi rows (N = 144 or
+//      224); lane (p, n) forms G_{n,lm} and its partial contraction; thread
 //      (p, i) sums the five n in a fixed order and writes the per-atom
-//      tensor.
+//      tensor.  The next round's copy starts once this round's products
+//      have read their buffer.
 // Each structure's per-atom results depend only on its atoms, so the usual
 // FP64 per-structure reduction follows.  All waits are bounded; on give-up
 // the CTA raises TNEP_ERR_TIMEOUT, issues nothing further, waits (bounded)
@@ -185,16 +190,16 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   extern __shared__ __align__(16) unsigned char smem[];
   float* qbuf = reinterpret_cast<float*>(smem + kOffQ);
   float* nsum = reinterpret_cast<float*>(smem + off_nsum<RANK>());
-  // mbarriers: 0 bulk loads, 1 phase-1 product, 2-3 X copies (one per
-  // buffer), 4-5 chunk products (one per TMEM buffer).  Each has at most one
-  // phase outstanding, so its k-th use completes with parity k & 1.
+  // mbarriers (each has at most one phase outstanding, so its k-th use
+  // completes with parity k & 1): bulk loads of the coefficient tile and B
+  // blocks (phase 1, again for phase 3), the first product, the X copy of
+  // each round, the weight blocks of phase 2, the products of each round
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffBar + 48);
   const uint32_t s_base = tc::smem_addr(smem);
   const uint32_t bar_load = tc::smem_addr(&bars[0]), bar_mma = tc::smem_addr(&bars[1]);
-  const uint32_t bar_x[2] = {tc::smem_addr(&bars[2]), tc::smem_addr(&bars[3])};
-  const uint32_t bar_c[2] = {tc::smem_addr(&bars[4]), tc::smem_addr(&bars[5])};
-  const uint32_t bar_w = bar_c[1];  // the weight blocks of phase 2 (the second product barrier is unused)
+  const uint32_t bar_x = tc::smem_addr(&bars[2]), bar_w = tc::smem_addr(&bars[3]);
+  const uint32_t bar_r = tc::smem_addr(&bars[4]);
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x / a.n_mt, mt = blockIdx.x % a.n_mt;
@@ -209,17 +214,17 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   auto x_src = [&](int i) { return a.mom_tc + (size_t)atom_of(i) * xs + kBBytes; };
   // thread 0: bulk copies of round r's X blocks (the zero block past the tile)
   auto load_round = [&](int r) {
-    tc::mbar_expect_tx(bar_x[0], AG * XB);
+    tc::mbar_expect_tx(bar_x, AG * XB);
     for (int ia = 0; ia < AG; ++ia) {
       const int i = AG * r + ia;
       tc::bulk_g2s(s_base + kOffX0 + ia * XB, i < kNT ? x_src(i) : a.mom_tc + (size_t)a.n_atoms * xs + kBBytes,
-                   XB, bar_x[0]);
+                   XB, bar_x);
     }
   };
 
   // ---------------------------------------------------------------- set-up
   if (tid == 0) {
-    for (int b = 0; b < 6; ++b) tc::mbar_init(tc::smem_addr(&bars[b]), 1);
+    for (int b = 0; b < 5; ++b) tc::mbar_init(tc::smem_addr(&bars[b]), 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), TCOLS);
@@ -229,8 +234,8 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
   const uint32_t tmem = *tslot;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
 
-  // issued by thread 0 and not yet observed complete (for the give-up path)
-  int n_commit = 0, x_issued[2] = {0, 0}, x_seen[2] = {0, 0}, c_issued[2] = {0, 0}, c_seen[2] = {0, 0};
+  // what thread 0 has issued and seen complete, per barrier (for the give-up path)
+  int n_commit = 0, x_issued = 0, x_seen = 0, r_issued = 0, r_seen = 0;
   int load_issued = 1, load_seen = 0;  // uses of bar_load: phase 1, then phase 3
   bool w_issued = false, w_seen = false;
   volatile int* s_flag = reinterpret_cast<volatile int*>(smem + kOffBar + 52);
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
     // phase's generic accesses before them
     tc::fence_proxy_async_smem();
     __syncthreads();
-    // reload the coefficient tile and the B blocks for phase 3, and the first X chunk
+    // reload the coefficient tile and the B blocks for phase 3, and round 0's X blocks
     if (tid == 0) {
       tc::mbar_expect_tx(bar_load, kCoefBytes + kNT * kBBytes);
       tc::bulk_g2s(s_base + kOffC, a.coef_tc + (size_t)(tau * a.n_mt + mt) * kCoefBytes, kCoefBytes, bar_load);
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
         tc::bulk_g2s(s_base + kOffB + i * kBBytes, a.mom_tc + (size_t)atom_of(i) * xs, kBBytes, bar_load);
       load_issued = 2;
       load_round(0);
-      ++x_issued[0];
+      ++x_issued;
     }
     // 2c. thread (p, atom x): radial part of Eqs. 3-4 through the moments V
     // (rank 1) or W (rank 2), and U on the diagonal (rank 2)
@@ -495,23 +500,23 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
     for (int r = 0; r < NROUND; ++r) {
       bool ok0 = okl;
       if (tid == 0 && ok0) {
-        ok0 = tc::mbar_wait_bounded(bar_x[0], r & 1, kTries);
+        ok0 = tc::mbar_wait_bounded(bar_x, r & 1, kTries);
         if (ok0) {
-          ++x_seen[0];
+          ++x_seen;
           tc::fence_after_sync();
           issue_split_products(tmem, s_base + kOffC, s_base + kOffB + 3 * AG * r * kGroup, tc::idesc_bf16_f32(128, AN));
           issue_split_products(tmem + AN, s_base + kOffC, s_base + kOffX0, tc::idesc_bf16_f32(128, XN));
-          tc::commit_to(bar_c[0]);
-          ++c_issued[0];
+          tc::commit_to(bar_r);
+          ++r_issued;
         }
       }
-      ok = __syncthreads_and(ok0 && tc::mbar_wait_bounded(bar_c[0], r & 1, kTries)) != 0;
+      ok = __syncthreads_and(ok0 && tc::mbar_wait_bounded(bar_r, r & 1, kTries)) != 0;
       if (!ok) goto give_up;
       if (tid == 0) {
-        ++c_seen[0];
+        ++r_seen;
         if (r + 1 < NROUND) {  // round r's products have read the buffer
           load_round(r + 1);
-          ++x_issued[0];
+          ++x_issued;
         }
       }
       tc::fence_after_sync();
@@ -579,17 +584,17 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
 
 give_up:
   // Nothing further is issued.  Thread 0 knows what it started: the bulk
-  // loads, the last committed product, and an X copy per buffer.  It waits
-  // (bounded) for each of them; TMEM is freed only if all arrived, so no late
-  // product can write columns another CTA has been given since.
+  // loads, the last committed product, the X copy and the weight blocks.  It
+  // waits (bounded) for each of them; TMEM is freed only if all arrived, so
+  // no late product can write columns another CTA has been given since, and
+  // no late copy can land in shared memory the CTA no longer owns.
   if (tid == 0) {
     if (a.status) atomicCAS(&a.status->error, 0, TNEP_ERR_TIMEOUT);
     bool drained = true;
     if (load_issued > load_seen) drained = tc::mbar_wait_bounded(bar_load, (load_issued - 1) & 1, kTries) && drained;
     if (n_commit > mma_done) drained = tc::mbar_wait_bounded(bar_mma, 0, kTries) && drained;
-    for (int b = 0; b < 2; ++b)
-      if (x_issued[b] > x_seen[b]) drained = tc::mbar_wait_bounded(bar_x[b], (x_issued[b] - 1) & 1, kTries) && drained;
-    if (c_issued[0] > c_seen[0]) drained = tc::mbar_wait_bounded(bar_c[0], (c_issued[0] - 1) & 1, kTries) && drained;
+    if (x_issued > x_seen) drained = tc::mbar_wait_bounded(bar_x, (x_issued - 1) & 1, kTries) && drained;
+    if (r_issued > r_seen) drained = tc::mbar_wait_bounded(bar_r, (r_issued - 1) & 1, kTries) && drained;
     if (w_issued && !w_seen) drained = tc::mbar_wait_bounded(bar_w, 0, kTries) && drained;
     *s_flag = drained ? 1 : 0;
   }
