@@ -353,7 +353,10 @@ tnep_status tnep_wait(tnep_server* server, uint64_t ticket, double* out, double 
 /* stats[6]: completed requests, batches launched, atoms evaluated, admitted bytes in use,
  * requests in flight, requests pending. */
 tnep_status tnep_server_stats(tnep_server* server, double stats[6]);
-/* Finishes admitted requests (bounded by their device work), then frees the server. */
+/* Finishes admitted requests (bounded by their device work), then frees the server.
+ * Calls on the server already in progress when the stop begins complete first
+ * (a submit is then either served or refused with TNEP_ERR_INVALID); no call
+ * may start on the server once tnep_server_stop has been called. */
 void tnep_server_stop(tnep_server* server);
 
 /* Polarized Raman (Sec. II.G).  The Stokes cross-section for observed
@@ -448,11 +451,17 @@ enum {
                                        TNEP_FAULT=oom@N set before the library is loaded, allocation number N
                                        fails once (nothing is allocated, the device is untouched) and the call
                                        making it returns TNEP_ERR_OOM; the context stays usable. */
-  TNEP_OPT_WAIT_TRIES = 13          /* try_wait limit of the device-side waits for the tensor-core network's
+  TNEP_OPT_WAIT_TRIES = 13,         /* try_wait limit of the device-side waits for the tensor-core network's
                                        products (default 4194304).  A CTA whose wait runs out stores nothing,
                                        waits (with the default limit) for its product to finish, frees its tensor
                                        memory and makes the call return TNEP_ERR_TIMEOUT; 0 makes every such
                                        wait give up at once (used to test that path).  The context stays usable. */
+  TNEP_OPT_PAIR_CACHE = 14          /* 1 (default): the fused kernel's forward walk over the angular list stores
+                                       each pair's r_ij, 1/|r_ij|, g_n and g_n' (64 bytes for the standard sizes)
+                                       in a device buffer of cap_A x 64 bytes per atom that its backward walk
+                                       reads back; 0: the backward walk recomputes them.  Results are the same
+                                       either way up to float32 rounding; skipped where the buffer would exceed
+                                       8 GB. */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

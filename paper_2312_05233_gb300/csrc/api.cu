@@ -170,6 +170,10 @@ tnep_status tnep_set_option(tnep_ctx* c, int option, double value) {
       if (!(value >= 0.0) || value > 9.0e15) return fail(TNEP_ERR_INVALID, "wait limit must be in [0, 9e15]");
       c->wait_tries = (long long)value;
       return TNEP_OK;
+    case TNEP_OPT_PAIR_CACHE:
+      if (value != 0.0 && value != 1.0) return fail(TNEP_ERR_INVALID, "pair cache must be 0 or 1");
+      c->pair_cache = (int)value;
+      return TNEP_OK;
     default:
       return fail(TNEP_ERR_INVALID, "unknown or read-only option");
   }
@@ -192,6 +196,7 @@ tnep_status tnep_get_option(const tnep_ctx* c, int option, double* value) {
     case TNEP_OPT_LAST_SKIN_USED: *value = c->last_skin_used; return TNEP_OK;
     case TNEP_OPT_ALLOC_COUNT: *value = (double)alloc_count(); return TNEP_OK;
     case TNEP_OPT_WAIT_TRIES: *value = (double)c->wait_tries; return TNEP_OK;
+    case TNEP_OPT_PAIR_CACHE: *value = c->pair_cache; return TNEP_OK;
     default: return fail(TNEP_ERR_INVALID, "unknown option");
   }
 }

@@ -398,11 +398,21 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
   TNEP_CUDA(w.per_atom.ensure(per_model * c->models.size()));
   TNEP_CUDA(w.out.ensure((size_t)std::max(S, 1) * total_C(c)));
   TNEP_TRY(compute_moments(c, w, st, N, any_rank(c, 1), any_rank(c, 2)));
+  // per-pair cache of the angular walks, reused by every model in turn
+  // (skipped when the lists' cap would make it larger than kPairCacheMaxBytes)
+  int quads = 0;
+  for (const auto& m : c->models) quads = std::max(quads, pair_cache_quads(m.d.n_max_A + 1));
+  const int pc_stride = round_up(std::max(N, 1), 128);
+  const size_t pc_elems = (size_t)w.cap_A * quads * pc_stride;
+  const bool use_pc = c->pair_cache && pc_elems * sizeof(float4) <= kPairCacheMaxBytes;
+  if (use_pc) TNEP_CUDA(w.pcache.ensure(pc_elems));
   for (size_t k = 0; k < c->models.size(); ++k) {
     const Model& m = c->models[k];
     FusedArgs f = fused_args(c, w, m, N);
     f.per_atom = w.per_atom.p + k * per_model;
     f.per_atom_stride = 0;
+    f.pcache = use_pc ? w.pcache.p : nullptr;
+    f.pc_stride = pc_stride;
     TNEP_CUDA(launch_fused(m.variant, m.d.rank, f, 1, c->block_atoms, m.d.mlp_precision, st));
   }
   if (ev_done) TNEP_CUDA(cudaEventRecord(ev_done, st));

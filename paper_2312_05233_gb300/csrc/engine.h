@@ -100,6 +100,7 @@ struct Workspace {
   DevBuf<int> sorted_orig, orig_sorted, sorted_struct, struct_cells, cnt_R, cnt_A, nbr_R, nbr_A;
   DevBuf<int> nbr_tmp, seg_R, struct_flags;
   DevBuf<float> mom;        // radial moments [slots][atom_stride]
+  DevBuf<float4> pcache;    // per-pair cache of the angular walk (see FusedArgs)
   int mom_v0 = -1, mom_w0 = -1;
   DevBuf<float4> pos4;
   DevBuf<StructGrid> grids;
@@ -122,7 +123,7 @@ struct Workspace {
                     &types_stage, &nbr_tmp, &seg_R, &struct_flags})
       b->release();
     pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release(); partial.release();
-    mom.release();
+    mom.release(); pcache.release();
     pos_stage[0].release(); pos_stage[1].release(); box_stage.release();
     if (d_status) cudaFree(d_status);
     d_status = nullptr;
@@ -168,6 +169,7 @@ struct tnep_ctx {
   int block_atoms = 128;  // atoms per CTA of the fused kernel (64 or 128)
   int population_form = 0;  // 0 = timed choice, 1 = per-pair walk, 2 = factored, 3 = factored on the tensor cores
   long long wait_tries = tnep::kDefaultWaitTries;  // bounded-wait limit of the tensor-core network
+  int pair_cache = 1;      // the fused kernel caches each angular pair's values between its walks
   double last_kernel_ms = 0.0;
   double last_nbr_ms = 0.0;
   int last_launches = 0;

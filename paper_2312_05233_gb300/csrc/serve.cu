@@ -68,7 +68,7 @@ struct Pipeline {
 // (positions, lists, moments, per-atom outputs).
 size_t bytes_per_atom(const tnep_ctx* c) {
   return 16 + 12 + 4 + (size_t)(2 * c->cap_R + c->cap_A) * 4 + (size_t)c->n_types * kMomBasis * 10 * 4 +
-         (size_t)9 * 4 * c->models.size() + 64;
+         (size_t)9 * 4 * c->models.size() + (c->pair_cache ? (size_t)c->cap_A * 4 * sizeof(float4) : 0) + 64;
 }
 
 }  // namespace
@@ -86,11 +86,19 @@ struct tnep_server {
   std::condition_variable cv_done, cv_work;
   std::thread worker;
   std::atomic<bool> stop{false};
+  std::atomic<int> callers{0};  // calls on the server in progress; stop waits for them
   uint64_t next_ticket = 1;
   uint64_t n_completed = 0, n_batches = 0, n_atoms_done = 0;
 };
 
 namespace {
+
+// Counts a call in progress for the lifetime of the guard.
+struct CallGuard {
+  tnep_server* s;
+  explicit CallGuard(tnep_server* srv) : s(srv) { if (s) s->callers.fetch_add(1); }
+  ~CallGuard() { if (s) s->callers.fetch_sub(1); }
+};
 
 void finish_request(tnep_server* s, const ReqPtr& r, tnep_status st) {
   r->status = st;
@@ -299,6 +307,7 @@ tnep_status tnep_server_start(tnep_ctx* ctx, size_t mem_budget_bytes, int max_sl
 }
 
 tnep_status tnep_submit(tnep_server* s, const tnep_request* req, uint64_t* ticket) {
+  CallGuard guard(s);
   if (!s || !req || !ticket) return fail(TNEP_ERR_INVALID, "NULL argument");
   if (s->stop.load()) return fail(TNEP_ERR_INVALID, "server is stopping");
   const int n = req->n_atoms;
@@ -318,6 +327,9 @@ tnep_status tnep_submit(tnep_server* s, const tnep_request* req, uint64_t* ticke
   r->bytes = (size_t)std::max(n, 1) * bytes_per_atom(s->ctx);
   {
     std::lock_guard<std::mutex> lock(s->mu);
+    // checked again under the lock the worker takes before it exits: a
+    // submit that races tnep_server_stop is either served or refused here
+    if (s->stop.load()) return fail(TNEP_ERR_INVALID, "server is stopping");
     if (s->n_inflight >= s->max_slots) return fail(TNEP_ERR_BUSY, "no free request slot");
     if (s->in_use + r->bytes > s->budget && s->n_inflight > 0)
       return fail(TNEP_ERR_BUSY, "device-memory budget exhausted");
@@ -359,6 +371,7 @@ static tnep_status take_result(tnep_server* s, uint64_t ticket, double* out, dou
 }
 
 tnep_status tnep_poll(tnep_server* s, uint64_t ticket, double* out, int* done, double* latency_s) {
+  CallGuard guard(s);
   if (!s || !done) return fail(TNEP_ERR_INVALID, "NULL argument");
   std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->table.find(ticket);
@@ -369,6 +382,7 @@ tnep_status tnep_poll(tnep_server* s, uint64_t ticket, double* out, int* done, d
 }
 
 tnep_status tnep_wait(tnep_server* s, uint64_t ticket, double* out, double timeout_s, double* latency_s) {
+  CallGuard guard(s);
   if (!s) return fail(TNEP_ERR_INVALID, "NULL argument");
   std::unique_lock<std::mutex> lock(s->mu);
   auto it = s->table.find(ticket);
@@ -383,6 +397,7 @@ tnep_status tnep_wait(tnep_server* s, uint64_t ticket, double* out, double timeo
 }
 
 tnep_status tnep_server_stats(tnep_server* s, double stats[6]) {
+  CallGuard guard(s);
   if (!s || !stats) return fail(TNEP_ERR_INVALID, "NULL argument");
   std::lock_guard<std::mutex> lock(s->mu);
   stats[0] = (double)s->n_completed;
@@ -399,14 +414,23 @@ void tnep_server_stop(tnep_server* s) {
   s->stop.store(true);
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
-  cudaSetDevice(s->ctx->device);
-  for (auto& p : s->pipes) {
-    if (p->stream) cudaStreamSynchronize(p->stream);
-    p->ws.release();
-    p->h_pos.release(); p->h_box.release(); p->h_types.release(); p->h_out.release();
-    p->d_pos.release(); p->d_box.release(); p->d_types.release();
-    if (p->done_ev) cudaEventDestroy(p->done_ev);
-    if (p->stream) cudaStreamDestroy(p->stream);
+  // every admitted request has finished, so waiting callers wake; calls
+  // already in progress return before the server is freed
+  while (s->callers.load() != 0) {
+    s->cv_done.notify_all();
+    std::this_thread::yield();
+  }
+  {
+    std::lock_guard<std::mutex> dl(s->dispatch_mu);  // a submit's own dispatch has finished
+    cudaSetDevice(s->ctx->device);
+    for (auto& p : s->pipes) {
+      if (p->stream) cudaStreamSynchronize(p->stream);
+      p->ws.release();
+      p->h_pos.release(); p->h_box.release(); p->h_types.release(); p->h_out.release();
+      p->d_pos.release(); p->d_box.release(); p->d_types.release();
+      if (p->done_ev) cudaEventDestroy(p->done_ev);
+      if (p->stream) cudaStreamDestroy(p->stream);
+    }
   }
   delete s;
 }

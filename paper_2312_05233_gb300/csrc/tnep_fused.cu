@@ -112,8 +112,13 @@ constexpr long long kMbarTries = kDefaultWaitTries;
 // list: A_nlm = sum_{t,k} c_nk B^t_{k,lm}, and -sum_{t,k,lm} H^t_{k,lm} Phi
 // (or Psi) with H^t_{k,lm} = sum_n G_nlm c_nk.  Exact up to rounding; used
 // for populations, whose individuals share the moments.
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, int TCM, bool FACT = false>
+// PC: the forward walk stores each pair's r_ij, 1/|r_ij|, g_n and g_n' in
+// a.pcache and the backward walk reads them back (bitwise the same values it
+// would recompute).
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int RANK, int BLK, int TCM, bool FACT = false,
+          bool PC = false>
 __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant__ FusedArgs a) {
+  static_assert(!(PC && FACT), "the pair cache belongs to the walked form");
   constexpr bool TC = TCM != 0;
   static_assert(!TC || BLK == 128, "the tensor-core network uses M = 128 rows, one per atom");
   constexpr int NLM = LMAX * (LMAX + 2);
@@ -264,17 +269,41 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float rinv = rsqrtf(r2);
       const float r = r2 * rinv;
-      float f[BA];
-      basis_fwd<BA>(r, rcAinv, f);
       float cc[NBA4];
       load_coeffs<NA, BA>(cA_i + __float_as_int(pj.w) * Ly.stride_cA, cc);
       float g[NA];
+      if constexpr (PC) {
+        // the backward walk's g_n and g_n', computed here once and cached
+        float f[BA], df[BA], dg[NA];
+        basis_fwd_bwd<BA>(r, rcAinv, f, df);
 #pragma unroll
-      for (int n = 0; n < NA; ++n) {
-        float s = 0.f;
+        for (int n = 0; n < NA; ++n) {
+          float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int k = 0; k < BA; ++k) s += cc[n * BA + k] * f[k];
-        g[n] = s;
+          for (int k = 0; k < BA; ++k) { s0 += cc[n * BA + k] * f[k]; s1 += cc[n * BA + k] * df[k]; }
+          g[n] = s0; dg[n] = s1;
+        }
+        constexpr int NQ = pair_cache_quads(NA);
+        float v[4 * NQ];
+        v[0] = dx; v[1] = dy; v[2] = dz; v[3] = rinv;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) { v[4 + n] = g[n]; v[4 + NA + n] = dg[n]; }
+#pragma unroll
+        for (int u = 4 + 2 * NA; u < 4 * NQ; ++u) v[u] = 0.f;
+        float4* dst = a.pcache + (size_t)kk * NQ * a.pc_stride + i_raw;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          __stcg(dst + (size_t)q * a.pc_stride, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+      } else {
+        float f[BA];
+        basis_fwd<BA>(r, rcAinv, f);
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+          float s = 0.f;
+#pragma unroll
+          for (int k = 0; k < BA; ++k) s += cc[n * BA + k] * f[k];
+          g[n] = s;
+        }
       }
       float p[NLM];
       real_harmonics<LMAX>(dx * rinv, dy * rinv, dz * rinv, p);
@@ -612,28 +641,56 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
         }
       }
     }
-    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, 0, FACT ? 0 : nA, pi);
-    for (int kk = 0; kk < (FACT ? 0 : nA); ++kk) {
-      const float4 pj = wB.next(kk);
-      const float dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
-      const float dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
-      const float dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      const float rinv = rsqrtf(r2);
-      const float r = r2 * rinv;
-      const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv;
-      float f[BA], df[BA];
-      basis_fwd_bwd<BA>(r, rcAinv, f, df);
-      float cc[NBA4];
-      load_coeffs<NA, BA>(cA_i + __float_as_int(pj.w) * Ly.stride_cA, cc);
-      float g[NA], dg[NA];
+    constexpr int NQ = pair_cache_quads(NA);
+    NbrWalk wB(a.nbr_A, a.pos4, i, a.cap_A, 0, (FACT || PC) ? 0 : nA, pi);
+    // cached pairs: the next pair's quads are loaded one iteration ahead
+    const float4* pcs = PC ? a.pcache + i_raw : nullptr;  // own slots also past the end (tensor-core path)
+    float4 nxt[PC ? NQ : 1];
+    if constexpr (PC) {
+      if (nA > 0) {
 #pragma unroll
-      for (int n = 0; n < NA; ++n) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int k = 0; k < BA; ++k) { s0 += cc[n * BA + k] * f[k]; s1 += cc[n * BA + k] * df[k]; }
-        g[n] = s0; dg[n] = s1;
+        for (int q = 0; q < NQ; ++q) nxt[q] = __ldcs(pcs + (size_t)q * a.pc_stride);
       }
+    }
+    for (int kk = 0; kk < (FACT ? 0 : nA); ++kk) {
+      float dx, dy, dz, rinv;
+      float g[NA], dg[NA];
+      if constexpr (PC) {
+        float v[4 * NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          v[4 * q] = nxt[q].x; v[4 * q + 1] = nxt[q].y; v[4 * q + 2] = nxt[q].z; v[4 * q + 3] = nxt[q].w;
+        }
+        if (kk + 1 < nA) {
+          const float4* src = pcs + (size_t)(kk + 1) * NQ * a.pc_stride;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) nxt[q] = __ldcs(src + (size_t)q * a.pc_stride);
+        }
+        dx = v[0]; dy = v[1]; dz = v[2]; rinv = v[3];
+#pragma unroll
+        for (int n = 0; n < NA; ++n) { g[n] = v[4 + n]; dg[n] = v[4 + NA + n]; }
+      } else {
+        const float4 pj = wB.next(kk);
+        dx = min_image(pj.x, pi.x, bx.L[0], bx.invL[0]);
+        dy = min_image(pj.y, pi.y, bx.L[1], bx.invL[1]);
+        dz = min_image(pj.z, pi.z, bx.L[2], bx.invL[2]);
+        const float r2w = dx * dx + dy * dy + dz * dz;
+        rinv = rsqrtf(r2w);
+        const float r = r2w * rinv;
+        float f[BA], df[BA];
+        basis_fwd_bwd<BA>(r, rcAinv, f, df);
+        float cc[NBA4];
+        load_coeffs<NA, BA>(cA_i + __float_as_int(pj.w) * Ly.stride_cA, cc);
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < BA; ++k) { s0 += cc[n * BA + k] * f[k]; s1 += cc[n * BA + k] * df[k]; }
+          g[n] = s0; dg[n] = s1;
+        }
+      }
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv;
       float p[NLM];
       real_harmonics<LMAX>(ux, uy, uz, p);
       // S_lm = sum_n G_nlm g_n; sum_lm T_lm p_lm = sum_n g'_n P_n with
@@ -697,13 +754,13 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
 }
 
-template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, int TCM, bool FACT = false>
+template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, int TCM, bool FACT = false, bool PC = false>
 cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
   const int nblk = (a.n_atoms + BLK - 1) / BLK;
   if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
-  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TCM, FACT>
-                      : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TCM, FACT>;
+  auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TCM, FACT, PC>
+                      : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TCM, FACT, PC>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, BLK, smem, st>>>(a);
@@ -716,6 +773,12 @@ cudaError_t launch_variant(int rank, const FusedArgs& a, int n_pop, int block, i
   if (a.amom && tcm == 0) {
     if (block == 64) return launch_block<NR, NA, BR, BA, LMAX, FB, 64, 0, true>(rank, a, n_pop, smem, st);
     return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 0, true>(rank, a, n_pop, smem, st);
+  }
+  // the pair cache holds one individual's pairs
+  if (a.pcache && n_pop == 1 && !a.amom && (block == 128 || tcm != 0)) {
+    if (tcm == 1) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 1, false, true>(rank, a, n_pop, smem, st);
+    if (tcm == 2) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 2, false, true>(rank, a, n_pop, smem, st);
+    return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 0, false, true>(rank, a, n_pop, smem, st);
   }
   if (tcm == 1) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 1>(rank, a, n_pop, smem, st);
   if (tcm == 2) return launch_block<NR, NA, BR, BA, LMAX, FB, 128, 2>(rank, a, n_pop, smem, st);

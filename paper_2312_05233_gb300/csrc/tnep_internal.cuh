@@ -170,7 +170,17 @@ struct FusedArgs {
   const float* amom; int amom_slots;   // angular moments (factored population path), else null
   DevStatus* status;         // error word (bounded waits of the tensor-core path)
   long long wait_tries;      // try_wait limit of the tensor-core network's product waits
+  // Per-pair cache of the angular walk (single-individual launches, else
+  // null): the forward walk stores, for pair k of atom i, r_ij and 1/|r_ij|,
+  // g_n and g_n' in pair_cache_quads(NA) float4 at
+  // pcache[(k * quads + q) * pc_stride + i]; the backward walk reads them back
+  // instead of repeating the neighbour gather, the minimum image, the basis
+  // and the coefficient sums.
+  float4* pcache;
+  int pc_stride;
 };
+__host__ __device__ constexpr int pair_cache_quads(int na) { return (4 + 2 * na + 3) / 4; }
+constexpr size_t kPairCacheMaxBytes = size_t(8) << 30;
 // Default try_wait limit of the device-side bounded waits.
 constexpr long long kDefaultWaitTries = 1LL << 22;
 

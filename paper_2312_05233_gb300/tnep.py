@@ -30,7 +30,8 @@ TNEP_SPECTRUM_IR, TNEP_SPECTRUM_RAMAN_ISO, TNEP_SPECTRUM_RAMAN_ANISO = 0, 1, 2
 (TNEP_OPT_FRAMES_PER_BATCH, TNEP_OPT_MAX_NEIGHBORS, TNEP_OPT_BLOCK_ATOMS, TNEP_OPT_LAST_KERNEL_MS,
  TNEP_OPT_CELL_DIV, TNEP_OPT_LAST_KERNEL_LAUNCHES, TNEP_OPT_LAST_NBR_MS,
  TNEP_OPT_KERNEL_LAUNCHES_TOTAL, TNEP_OPT_SKIN, TNEP_OPT_LAST_SKIN_USED,
- TNEP_OPT_POPULATION_FORM, TNEP_OPT_CELL_XDIV, TNEP_OPT_ALLOC_COUNT, TNEP_OPT_WAIT_TRIES) = range(14)
+ TNEP_OPT_POPULATION_FORM, TNEP_OPT_CELL_XDIV, TNEP_OPT_ALLOC_COUNT, TNEP_OPT_WAIT_TRIES,
+ TNEP_OPT_PAIR_CACHE) = range(15)
 
 # Every symbol include/tnep.h declares (tests check the library exports them).
 EXPORTED = [

@@ -716,6 +716,33 @@ def test_tensor_core_network(tn, small, n_types):
         assert not np.array_equal(outs[2][k], outs[1][k])
 
 
+@pytest.mark.parametrize("small,n_types", [(False, 2), (True, 3)])
+def test_pair_cache_equals_recomputed_walk(tn, small, n_types):
+    """The backward walk reads each pair's r_ij, 1/|r_ij|, g_n and g_n' from
+    the cache the forward walk wrote, or recomputes them: the same values, so
+    the results agree bit for bit, for every network mode and with a partly
+    filled last CTA (192 and 135 atoms)."""
+    if n_types == 2:
+        frames, types, box = synth.water_small(4)
+    else:
+        rng = np.random.default_rng(8)
+        base, types, box = synth.bzo_supercell(3)
+        frames = synth.thermal_frames(base, box, 3, 0.08, rng)
+        box = box.astype(np.float32)
+    ms32, om = models_for(tn, n_types, small=small)
+    for mode in (0, 1, 2):
+        c = tn.tnep_create(with_precision(tn, ms32, mode, n_types), n_types, RC)
+        assert tn.tnep_get_option(c, tn.TNEP_OPT_PAIR_CACHE) == 1
+        on = tn.tnep_eval(c, frames, box, types)
+        tn.tnep_set_option(c, tn.TNEP_OPT_PAIR_CACHE, 0)
+        off = tn.tnep_eval(c, frames, box, types)
+        for a, b in zip(on, off):
+            assert np.array_equal(a, b), mode
+        c.close()
+    res = oracle.evaluate(om[0], frames[0], box, types)
+    assert np.linalg.norm(on[0][0] - res.tensor) <= bf16_bound(res)
+
+
 def test_tensor_core_network_perovskite_full_size(tn):
     """BaZrO3 12x12x12 (8,640 atoms, 3 types), rank-2 susceptibility, the
     precision workload: whole frames through the oracle.  BF16 network (mode

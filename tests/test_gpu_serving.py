@@ -97,3 +97,40 @@ def test_admission_budget_slots_and_timeout(tn):
         else:  # the first one already finished
             srv.wait(t2)
     ctx.close()
+
+
+def test_stop_finishes_admitted_requests_and_waiting_calls(tn):
+    """A wait in progress when the stop begins returns its result: the stop
+    finishes every admitted request and lets calls in progress return before
+    it frees the server."""
+    import threading
+    import time
+    ms, _ = six_type_models(tn)
+    ctx = tn.tnep_create(ms[:1], 6, RC)
+    frames, types, box = synth.water_bulk(n_frames=1)
+    wtypes = np.where(types == 0, 3, 0).astype(np.int32)
+    shifts = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], np.float32) * box
+    big_pos = (frames[0][None] + shifts[:, None]).reshape(-1, 3)
+    big_types = np.tile(wtypes, 8)
+    plain, _ = tn.tnep_eval_batch(ctx, [0, len(big_types)], big_pos, (2 * box)[None], big_types)
+    srv = tn.tnep_server_start(ctx, mem_budget_bytes=96 << 30, n_pipelines=1, max_batch_atoms=len(big_types))
+    # queued one batch at a time on one pipeline: tens of milliseconds of work
+    tickets = [srv.submit(big_pos, big_types, 2 * box) for _ in range(24)]
+    assert all(t is not None for t in tickets)
+    entered, got = threading.Event(), {}
+
+    def waiter():
+        entered.set()
+        got["out"], got["lat"] = srv.wait(tickets[-1], timeout_s=120.0)
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    entered.wait()
+    time.sleep(0.02)  # the waiter is blocked inside the call
+    t0 = time.perf_counter()
+    srv.stop()
+    th.join(timeout=120.0)
+    assert not th.is_alive()
+    assert np.array_equal(got["out"], plain[0][0])
+    assert got["lat"] > 0 and time.perf_counter() - t0 < 120.0
+    ctx.close()
