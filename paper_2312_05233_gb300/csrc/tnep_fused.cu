@@ -661,6 +661,12 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
         for (int q = 0; q < NQ; ++q) {
           v[4 * q] = nxt[q].x; v[4 * q + 1] = nxt[q].y; v[4 * q + 2] = nxt[q].z; v[4 * q + 3] = nxt[q].w;
         }
+        // pair kk + 2 towards L1 (the register copy is one pair ahead)
+        if (kk + 2 < nA) {
+          const float4* pf = pcs + (size_t)(kk + 2) * NQ * a.pc_stride;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) asm volatile("prefetch.global.L1 [%0];" ::"l"(pf + (size_t)q * a.pc_stride));
+        }
         if (kk + 1 < nA) {
           const float4* src = pcs + (size_t)(kk + 1) * NQ * a.pc_stride;
 #pragma unroll
