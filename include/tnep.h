@@ -460,8 +460,7 @@ enum {
                                        each pair's r_ij, 1/|r_ij|, g_n and g_n' (64 bytes for the standard sizes)
                                        in a device buffer of cap_A x 64 bytes per atom that its backward walk
                                        reads back; 0: the backward walk recomputes them.  Results are the same
-                                       either way up to float32 rounding; skipped where the buffer would exceed
-                                       8 GB. */
+                                       either way (bit for bit); skipped where the buffer would exceed 16 GB. */
 };
 tnep_status tnep_set_option(tnep_ctx* ctx, int option, double value);
 tnep_status tnep_get_option(const tnep_ctx* ctx, int option, double* value);

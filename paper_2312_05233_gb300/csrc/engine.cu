@@ -399,7 +399,9 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
   TNEP_CUDA(w.out.ensure((size_t)std::max(S, 1) * total_C(c)));
   TNEP_TRY(compute_moments(c, w, st, N, any_rank(c, 1), any_rank(c, 2)));
   // per-pair cache of the angular walks, reused by every model in turn
-  // (skipped when the lists' cap would make it larger than kPairCacheMaxBytes)
+  // (skipped when the lists' cap would make it larger than 16 GB: a pass of
+  // 2^21 atoms at cap_A = 64 takes 8.6 GB)
+  constexpr size_t kPairCacheMaxBytes = size_t(16) << 30;
   int quads = 0;
   for (const auto& m : c->models) quads = std::max(quads, pair_cache_quads(m.d.n_max_A + 1));
   const int pc_stride = round_up(std::max(N, 1), 128);

@@ -27,7 +27,8 @@
 //      its operands, the 25 individuals' W0 blocks are bulk-copied over them.
 //   2. thread (p, i): radial descriptor from the radial moments; the FP32
 //      network (Eq. 1) on the staged weights (b0, w1 in the rows' padding
-//      columns), dU/dq written over the descriptor row; the radial part of
+//      columns; packed multiply-adds over descriptor pairs), dU/dq written
+//      over the descriptor row; the radial part of
 //      Eqs. 3-4.  Meanwhile the coefficient tile and the B blocks are loaded
 //      again, with the first round's Phi / Psi blocks.
 //   3. rounds of AG atoms (2 for rank 1, 1 for rank 2): the product A again
@@ -52,6 +53,9 @@ namespace tnep {
 
 namespace {
 
+// hidden units per iteration of the per-thread network loop (best of 1, 2,
+// 3, 5, 6 measured)
+constexpr int kNetUnroll = 6;
 constexpr int kPT = kPopTcIndividuals;  // individuals per 128-row tile (125 rows used)
 constexpr int kNT = kPopTcAtoms;        // atoms per CTA
 constexpr int kKW = 96;                 // bf16 per operand row: three terms x K = 32
@@ -392,7 +396,11 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
         for (int d = 0; d < DP; ++d) e[d] = 0.f;
         float U = -__ldg(model + Ly.off_b1 + net);
         const unsigned char* Wp = smem + pl * kW0Stride;
-#pragma unroll 2
+        // z and e in descriptor pairs, one packed multiply-add per pair
+        f32x2 s2[15], e2[15];
+#pragma unroll
+        for (int v = 0; v < 15; ++v) { s2[v] = pk2(sv[2 * v], sv[2 * v + 1]); e2[v] = 0ull; }
+#pragma unroll kNetUnroll
         for (int h = 0; h < H; ++h) {
           const float4* w4 = reinterpret_cast<const float4*>(Wp + h * 128);
           float w[DP];
@@ -401,17 +409,23 @@ __global__ void __launch_bounds__(128, 2) k_pop_tc(const __grid_constant__ PopTc
             const float4 t4 = w4[v];
             w[4 * v] = t4.x; w[4 * v + 1] = t4.y; w[4 * v + 2] = t4.z; w[4 * v + 3] = t4.w;
           }
-          float zp[4] = {0.f, 0.f, 0.f, 0.f};
+          f32x2 z2[2] = {0ull, 0ull};
 #pragma unroll
-          for (int d = 0; d < 30; ++d) zp[d & 3] += w[d] * sv[d];
-          const float z = ((zp[0] + zp[1]) + (zp[2] + zp[3])) - w[30];
+          for (int v = 0; v < 15; ++v) z2[v & 1] = fma2(pk2(w[2 * v], w[2 * v + 1]), s2[v], z2[v & 1]);
+          float za, zb, zc, zd;
+          unpk2(z2[0], za, zb);
+          unpk2(z2[1], zc, zd);
+          const float z = ((za + zb) + (zc + zd)) - w[30];
           const float hh = tanhf(z);
           const float w1h = w[31];
           U += w1h * hh;
           const float vh = w1h * (1.f - hh * hh);
+          const f32x2 vv = pk2(vh, vh);
 #pragma unroll
-          for (int d = 0; d < 30; ++d) e[d] += vh * w[d];
+          for (int v = 0; v < 15; ++v) e2[v] = fma2(vv, pk2(w[2 * v], w[2 * v + 1]), e2[v]);
         }
+#pragma unroll
+        for (int v = 0; v < 15; ++v) unpk2(e2[v], e[2 * v], e[2 * v + 1]);
         float scl[DP];
         const float4* sc4 = reinterpret_cast<const float4*>(model + Ly.off_scaler);
 #pragma unroll

@@ -180,7 +180,6 @@ struct FusedArgs {
   int pc_stride;
 };
 __host__ __device__ constexpr int pair_cache_quads(int na) { return (4 + 2 * na + 3) / 4; }
-constexpr size_t kPairCacheMaxBytes = size_t(8) << 30;
 // Default try_wait limit of the device-side bounded waits.
 constexpr long long kDefaultWaitTries = 1LL << 22;
 
