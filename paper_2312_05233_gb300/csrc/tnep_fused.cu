@@ -29,7 +29,9 @@
 // C4 = (2 2 2; 0 0 0) (5 / 4 pi)^(3/2) / (2/9) (evaluate both sides at
 // a = b = c = z_hat; the invariant is unique up to scale).
 
+#include <algorithm>
 #include <atomic>
+#include <climits>
 
 #include "tc_sm100.cuh"
 #include "tnep_device.cuh"
@@ -130,52 +132,24 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   extern __shared__ float4 sm4[];
   float* sm = reinterpret_cast<float*>(sm4);
   const ModelLayout& Ly = a.lay;
-  // CTA -> (atom block, individual); with pop_major the individual varies
-  // fastest so that CTAs running together share an atom block's lists.
-  const int pop = a.pop_major ? blockIdx.x : blockIdx.y;
-  const int ablk = a.pop_major ? blockIdx.y : blockIdx.x;
-  {
-    const float4* src = reinterpret_cast<const float4*>(a.model + (size_t)pop * a.model_stride);
-    for (int k = threadIdx.x; k < (Ly.words >> 2); k += blockDim.x) sm4[k] = src[k];
-  }
-  __syncthreads();
   const int tid = threadIdx.x;
   float* scratch = sm + Ly.words + tid;  // slot s at scratch[s * BLK]
-  const int i_raw = ablk * BLK + tid;
-  const bool valid = i_raw < a.n_atoms;
-  // The tensor-core path has CTA-wide barriers: threads past the end work on
-  // the last atom and store nothing.
-  if (!TC && !valid) return;
-  const int i = valid ? i_raw : a.n_atoms - 1;
 
-  // ---------------------------------------------------------------- tensor-core set-up
+  // ---------------------------------------------------------------- tensor-core set-up (once per CTA)
   uint32_t tmem_base = 0, mbar = 0;
   __nv_bfloat16* tileA = nullptr;
-  const __nv_bfloat16* tileB1 = nullptr;
-  const __nv_bfloat16* tileB2 = nullptr;
+  __nv_bfloat16* tileB1 = nullptr;
+  __nv_bfloat16* tileB2 = nullptr;
+  int* next_item = nullptr;  // the CTA's next work item (tensor-core path)
   if constexpr (TC) {
     constexpr int NSLOT = NA * LMAX * (LMAX + 2);
     unsigned char* tcb = reinterpret_cast<unsigned char*>(sm + Ly.words + NSLOT * BLK);
     uint64_t* mb = reinterpret_cast<uint64_t*>(tcb);
     uint32_t* slot = reinterpret_cast<uint32_t*>(tcb + 8);
+    next_item = reinterpret_cast<int*>(tcb + 16);
     tileA = reinterpret_cast<__nv_bfloat16*>(tcb + 128);
-    __nv_bfloat16* B1 = tileA + 128 * 64;
-    __nv_bfloat16* B2 = B1 + Ly.nets * 32 * 64;
-    // B1[net]: row = hidden unit h, column = descriptor d  (W0[h][d])
-    // B2[net]: row = descriptor d, column = hidden unit h  (W0[h][d])
-    // columns 0-31 hold the bf16 rounding of the weight, 32-63 the bf16
-    // rounding of what is left over
-    for (int idx = tid; idx < Ly.nets * 32 * 32; idx += BLK) {
-      const int nt = idx >> 10, r = (idx >> 5) & 31, k = idx & 31;
-      const float* W = sm + Ly.off_W0 + nt * Ly.H * DP;
-      const float w1v = (r < Ly.H && k < Ly.D) ? W[r * DP + k] : 0.f;
-      const float w2v = (k < Ly.H && r < Ly.D) ? W[k * DP + r] : 0.f;
-      const __nv_bfloat16 h1 = __float2bfloat16_rn(w1v), h2 = __float2bfloat16_rn(w2v);
-      B1[nt * 2048 + (tc::kmajor_offset(r, k, 64) >> 1)] = h1;
-      B1[nt * 2048 + (tc::kmajor_offset(r, 32 + k, 64) >> 1)] = __float2bfloat16_rn(w1v - __bfloat162float(h1));
-      B2[nt * 2048 + (tc::kmajor_offset(r, k, 64) >> 1)] = h2;
-      B2[nt * 2048 + (tc::kmajor_offset(r, 32 + k, 64) >> 1)] = __float2bfloat16_rn(w2v - __bfloat162float(h2));
-    }
+    tileB1 = tileA + 128 * 64;
+    tileB2 = tileB1 + Ly.nets * 32 * 64;
     if (tid == 0) {
       tc::mbar_init(tc::smem_addr(mb), 1);
       tc::fence_mbar_init();
@@ -186,9 +160,57 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     tc::fence_after_sync();
     tmem_base = *slot;
     mbar = tc::smem_addr(mb);
-    tileB1 = B1;
-    tileB2 = B2;
   }
+
+  // Work item w = (atom block, individual); with pop_major the individual
+  // varies fastest so that CTAs running together share an atom block's lists.
+  // Without the tensor cores each CTA takes item blockIdx.x.  With them the
+  // CTAs are persistent: each starts with item blockIdx.x and takes the next
+  // from the counter a.status->work_next (gridDim.x + its value, zeroed before
+  // the launch), fetched by thread 0 between the two network products and
+  // handed to the CTA through shared memory across the second product's
+  // barrier; the model, the weight tiles made from it, the mbarrier and the
+  // TMEM columns are then set up once per CTA (the model again only when the
+  // individual changes).  Extra CTAs find the counter exhausted and exit, so
+  // the grid need not match the number of CTAs resident at once.
+  const int nblk = (a.n_atoms + BLK - 1) / BLK;
+  const int n_work = nblk * a.n_pop;
+  // loads individual `pop`'s model into shared memory (and, with the tensor
+  // cores, the weight tiles made from it)
+  auto load_model = [&](const int pop) {
+    const float4* src = reinterpret_cast<const float4*>(a.model + (size_t)pop * a.model_stride);
+    for (int k = tid; k < (Ly.words >> 2); k += BLK) sm4[k] = src[k];
+    __syncthreads();
+    if constexpr (TC) {
+      // B1[net]: row = hidden unit h, column = descriptor d  (W0[h][d])
+      // B2[net]: row = descriptor d, column = hidden unit h  (W0[h][d])
+      // columns 0-31 hold the bf16 rounding of the weight, 32-63 the bf16
+      // rounding of what is left over
+      for (int idx = tid; idx < Ly.nets * 32 * 32; idx += BLK) {
+        const int nt = idx >> 10, r = (idx >> 5) & 31, k = idx & 31;
+        const float* W = sm + Ly.off_W0 + nt * Ly.H * DP;
+        const float w1v = (r < Ly.H && k < Ly.D) ? W[r * DP + k] : 0.f;
+        const float w2v = (k < Ly.H && r < Ly.D) ? W[k * DP + r] : 0.f;
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(w1v), h2 = __float2bfloat16_rn(w2v);
+        tileB1[nt * 2048 + (tc::kmajor_offset(r, k, 64) >> 1)] = h1;
+        tileB1[nt * 2048 + (tc::kmajor_offset(r, 32 + k, 64) >> 1)] = __float2bfloat16_rn(w1v - __bfloat162float(h1));
+        tileB2[nt * 2048 + (tc::kmajor_offset(r, k, 64) >> 1)] = h2;
+        tileB2[nt * 2048 + (tc::kmajor_offset(r, 32 + k, 64) >> 1)] = __float2bfloat16_rn(w2v - __bfloat162float(h2));
+      }
+      // the tiles are made visible to the tensor cores by the fence and the
+      // barrier that precede every product
+    }
+  };
+
+  // one work item; false when the tensor-core network gave up (the CTA then
+  // returns at once)
+  auto item = [&](const int pop, const int ablk) -> bool {
+  const int i_raw = ablk * BLK + tid;
+  const bool valid = i_raw < a.n_atoms;
+  // The tensor-core path has CTA-wide barriers: threads past the end work on
+  // the last atom and store nothing.
+  if (!TC && !valid) return true;
+  const int i = valid ? i_raw : a.n_atoms - 1;
 
   const float4 pi = a.pos4[i];
   const int ti = __float_as_int(pi.w);
@@ -427,6 +449,9 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
     bool ok = gemm(tileB1, 0);
     float z[32];
     if (ok) {
+      // the next work item; its latency is hidden behind the network
+      int nxt = 0;
+      if (tid == 0) nxt = (int)gridDim.x + atomicAdd(&a.status->work_next, 1);
 #pragma unroll
       for (int k = 0; k < 32; ++k) z[k] = 0.f;
       read_row(z);
@@ -446,6 +471,9 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       // issued after the CTA-wide barrier in gemm, i.e. after every warp's
       // tcgen05.ld (each followed by tcgen05.wait::ld) above
       write_row(buf);
+      // published before the second product's barrier; read after the item,
+      // and rewritten only after the next item's first barrier
+      if (tid == 0) *next_item = nxt;
       pending = 1;
       ok = gemm(tileB2, 1);
     }
@@ -458,16 +486,13 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
         __syncthreads();
         if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
       }
-      return;
+      return false;
     }
 #pragma unroll
     for (int k = 0; k < 32; ++k) z[k] = 0.f;
     read_row(z);
 #pragma unroll
     for (int d = 0; d < DP; ++d) e[d] = z[d] * sc[d];
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
   } else if constexpr (FACT) {
     // scalar products: measured faster than the packed form below in the
     // factored population kernel
@@ -753,22 +778,68 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   }
 
   // ---------------------------------------------------------------- per-atom output
-  if (!valid) return;
-  float* out = a.per_atom + (size_t)pop * a.per_atom_stride;
-  if constexpr (RANK == 2) { acc[0] += U; acc[4] += U; acc[8] += U; }
+  if (valid) {
+    float* out = a.per_atom + (size_t)pop * a.per_atom_stride;
+    if constexpr (RANK == 2) { acc[0] += U; acc[4] += U; acc[8] += U; }
 #pragma unroll
-  for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
+    for (int c = 0; c < C; ++c) out[(size_t)c * a.atom_stride + i] = acc[c];
+  }
+  return true;
+  };
+
+  if constexpr (TC) {
+    int loaded = -1;
+    for (int wi = blockIdx.x; wi < n_work;) {
+      const int pop = a.pop_major ? wi % a.n_pop : wi / nblk;
+      const int ablk = a.pop_major ? wi / a.n_pop : wi % nblk;
+      if (pop != loaded) {
+        __syncthreads();  // every thread is done with the previous model and tiles
+        load_model(pop);
+        loaded = pop;
+      }
+      if (!item(pop, ablk)) return;
+      wi = *next_item;
+    }
+    // every warp's last tcgen05.ld has completed (tcgen05.wait::ld in tmem_ld32)
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tmem_base, tc_tmem_cols(Ly.nets));
+  } else {
+    // grid (atom blocks, individuals), or (individuals, atom blocks) with pop_major
+    const int pop = a.pop_major ? blockIdx.x : blockIdx.y;
+    load_model(pop);
+    item(pop, a.pop_major ? blockIdx.y : blockIdx.x);
+  }
 }
 
+// One CTA per work item (atom block, individual), or, for the tensor-core
+// network, persistent CTAs: two per SM (what fits; the runtime's occupancy
+// figure for this kernel is one, but two are resident), extra ones exit at once.
 template <int NR, int NA, int BR, int BA, int LMAX, bool FB, int BLK, int TCM, bool FACT = false, bool PC = false>
-cudaError_t launch_block(int rank, const FusedArgs& a, int n_pop, size_t smem, cudaStream_t st) {
-  const int nblk = (a.n_atoms + BLK - 1) / BLK;
-  if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
-  const dim3 grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
+cudaError_t launch_block(int rank, const FusedArgs& a_in, int n_pop, size_t smem, cudaStream_t st) {
+  FusedArgs a = a_in;
+  a.n_pop = n_pop;
+  const long long n_work = (long long)((a.n_atoms + BLK - 1) / BLK) * n_pop;
+  if (n_work > INT_MAX) return cudaErrorInvalidConfiguration;
   auto fn = rank == 1 ? k_fused<NR, NA, BR, BA, LMAX, FB, 1, BLK, TCM, FACT, PC>
                       : k_fused<NR, NA, BR, BA, LMAX, FB, 2, BLK, TCM, FACT, PC>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  dim3 grid;
+  if constexpr (TCM != 0) {
+    if (!a.status) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    grid = dim3((unsigned)std::min<long long>(n_work, 2LL * sms));
+    e = cudaMemsetAsync(&a.status->work_next, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  } else {
+    const int nblk = (a.n_atoms + BLK - 1) / BLK;
+    if (a.pop_major && nblk > 65535) return cudaErrorInvalidConfiguration;
+    if (!a.pop_major && n_pop > 65535) return cudaErrorInvalidConfiguration;
+    grid = a.pop_major ? dim3(n_pop, nblk) : dim3(nblk, n_pop);
+  }
   fn<<<grid, BLK, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ struct DevStatus {
   int max_cnt_R;    // largest radial neighbour count seen above the cap
   int max_cnt_A;    // largest angular neighbour count seen above the cap
   int skin_violation;  // an atom moved more than skin / 2 (or the box changed) within a pass
+  int work_next;    // work counter of the persistent fused kernel (zeroed before each of its launches)
 };
 
 // Per-structure cell grid (orthorhombic, periodic or open per axis).
@@ -166,7 +167,8 @@ struct FusedArgs {
   float* per_atom;           // [pop][C][atom_stride] (SoA, sorted order)
   size_t per_atom_stride;    // floats between individuals
   int atom_stride;           // row stride of the SoA output
-  int pop_major;             // 1: blockIdx.x = individual, blockIdx.y = atom block
+  int pop_major;             // 1: the individual varies fastest over the work items
+  int n_pop;                 // individuals (set by the launcher)
   const float* amom; int amom_slots;   // angular moments (factored population path), else null
   DevStatus* status;         // error word (bounded waits of the tensor-core path)
   long long wait_tries;      // try_wait limit of the tensor-core network's product waits
