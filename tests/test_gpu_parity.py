@@ -794,6 +794,33 @@ def test_tensor_core_population_and_tail_block(tn):
         ctx.close()
 
 
+def test_tensor_core_persistent_items_switch_individuals(tn):
+    """The tensor-core fused kernel runs persistent CTAs that take work items
+    (atom block, individual) from a counter and reload the model when the
+    individual changes: with more items than CTAs, every individual of a
+    population equals a single-model evaluation with its own parameters."""
+    rng = np.random.default_rng(21)
+    structs = synth.population_structures(n_clusters=40, n_boxes=6, seed_k=4)
+    bt = synth.concat_structures(structs)
+    hp = synth.HyperParams(n_types=2, rank=2)
+    sc = synth.default_q_scaler(hp)
+    n_pop = 7
+    params = np.stack([synth.model_params(hp, rng) for _ in range(n_pop)])
+    target = rng.standard_normal((bt.n_structs, 9))
+    assert n_pop * ((len(bt.types) + 127) // 128) > 2 * 152
+    for mode in (1, 2):
+        ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0], sc, mlp_precision=mode)], 2, RC)
+        _, pred = tn.tnep_eval_population(ctx, 0, params, bt.offsets, bt.pos, bt.box, bt.types, target,
+                                          want_out=True)
+        ctx.close()
+        for p in range(n_pop):
+            c1 = tn.tnep_create([tn.Model.from_hyper(hp, params[p], sc, mlp_precision=mode)], 2, RC)
+            (one,), _ = tn.tnep_eval_batch(c1, bt.offsets, bt.pos, bt.box, bt.types)
+            c1.close()
+            one = np.asarray(one)
+            assert np.all(np.abs(pred[p] - one) <= 1e-12 * np.abs(one).max()), (mode, p)
+
+
 # ------------------------------------------------------------ Verlet skin
 def _walk(n_side, L, n_frames, sigma, seed):
     rng = np.random.default_rng(seed)
