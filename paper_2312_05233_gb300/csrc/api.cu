@@ -58,6 +58,9 @@ tnep_status tnep_create(const tnep_model_desc* models, int n_models, int n_types
   };
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->red_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fused, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_reduced, cudaEventDisableTiming);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_consumed[k], cudaEventDisableTiming);
@@ -106,6 +109,7 @@ void tnep_destroy(tnep_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  if (c->red_stream) cudaStreamSynchronize(c->red_stream);
   for (auto& m : c->models)
     if (m.d_packed) cudaFree(m.d_packed);
   c->ws.release();
@@ -125,6 +129,9 @@ void tnep_destroy(tnep_ctx* c) {
   for (auto e : c->ev_pass) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->red_stream) cudaStreamDestroy(c->red_stream);
+  if (c->ev_fused) cudaEventDestroy(c->ev_fused);
+  if (c->ev_reduced) cudaEventDestroy(c->ev_reduced);
   delete c;
 }
 
@@ -264,16 +271,21 @@ tnep_status tnep_eval(tnep_ctx* c, int n_frames, int n_atoms, const float* pos, 
         TNEP_TRY(build_lists(c, c->ws, st, nf, offs.data(), d_pos, d_box, d_types, n_atoms));
       if (!pos_dev && n_atoms > 0) TNEP_CUDA(cudaEventRecord(c->ev_consumed[b & 1], st));
       TNEP_CUDA(cudaEventRecord(ev[1], st));
-      TNEP_TRY(run_models(c, c->ws, st, nf, nf * n_atoms, ev[2]));
+      // the pass's per-frame sums and their copy-out run on the side stream,
+      // overlapping the next pass's cell lists and neighbour build
+      TNEP_TRY(run_models(c, c->ws, st, nf, nf * n_atoms, ev[2], nullptr, c->red_stream));
       // scatter results: model m block [n_frames][C_m]
       size_t src_off = 0, dst_base = 0;
       for (const auto& m : c->models) {
         double* dst = out_dev ? out : c->h_out.p;
-        TNEP_TRY(copy_out(dst + dst_base + (size_t)f0 * m.C, c->ws.out.p + src_off, (size_t)nf * m.C, st));
+        TNEP_TRY(copy_out(dst + dst_base + (size_t)f0 * m.C, c->ws.out.p + src_off, (size_t)nf * m.C,
+                          c->red_stream));
         src_off += (size_t)nf * m.C;
         dst_base += (size_t)n_frames * m.C;
       }
+      TNEP_CUDA(cudaEventRecord(c->ev_reduced, c->red_stream));
     }
+    TNEP_CUDA(cudaStreamWaitEvent(st, c->ev_reduced, 0));
     if (use_skin) {
       TNEP_CUDA(cudaMemcpyAsync(c->skin_ws.h_status.p, c->skin_ws.d_status, sizeof(DevStatus),
                                 cudaMemcpyDeviceToHost, st));

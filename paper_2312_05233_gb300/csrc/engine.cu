@@ -393,7 +393,7 @@ tnep_status sum_pass_times(tnep_ctx* c, int n_pass) {
 }
 
 tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done,
-                       const unsigned char* ghost) {
+                       const unsigned char* ghost, cudaStream_t red_st) {
   const size_t per_model = (size_t)9 * w.atom_stride;
   TNEP_CUDA(w.per_atom.ensure(per_model * c->models.size()));
   TNEP_CUDA(w.out.ensure((size_t)std::max(S, 1) * total_C(c)));
@@ -408,6 +408,15 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
   const size_t pc_elems = (size_t)w.cap_A * quads * pc_stride;
   const bool use_pc = c->pair_cache && pc_elems * sizeof(float4) <= kPairCacheMaxBytes;
   if (use_pc) TNEP_CUDA(w.pcache.ensure(pc_elems));
+  const int* offsets = w.offsets.p;
+  if (red_st) {
+    // the previous pass's sums have read the per-atom outputs and offsets
+    TNEP_CUDA(cudaStreamWaitEvent(st, c->ev_reduced, 0));
+    TNEP_CUDA(w.red_offsets.ensure((size_t)S + 1));
+    TNEP_CUDA(cudaMemcpyAsync(w.red_offsets.p, w.offsets.p, sizeof(int) * ((size_t)S + 1), cudaMemcpyDeviceToDevice,
+                              st));
+    offsets = w.red_offsets.p;
+  }
   for (size_t k = 0; k < c->models.size(); ++k) {
     const Model& m = c->models[k];
     FusedArgs f = fused_args(c, w, m, N);
@@ -423,11 +432,17 @@ tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N,
       TNEP_CUDA(launch_zero_ghosts(N, w.sorted_orig.p, ghost, w.per_atom.p + k * per_model, w.atom_stride,
                                    c->models[k].C, st));
   TNEP_CUDA(w.partial.ensure((size_t)std::max(S, 1) * reduce_chunks(w.max_atoms) * 9));
+  cudaStream_t rs = st;
+  if (red_st) {
+    TNEP_CUDA(cudaEventRecord(c->ev_fused, st));
+    TNEP_CUDA(cudaStreamWaitEvent(red_st, c->ev_fused, 0));
+    rs = red_st;
+  }
   size_t off = 0;
   for (size_t k = 0; k < c->models.size(); ++k) {
     const Model& m = c->models[k];
-    TNEP_CUDA(launch_reduce(S, 1, w.offsets.p, w.max_atoms, w.per_atom.p + k * per_model, 0, w.atom_stride, m.C,
-                            w.partial.p, w.out.p + off, 0, st));
+    TNEP_CUDA(launch_reduce(S, 1, offsets, w.max_atoms, w.per_atom.p + k * per_model, 0, w.atom_stride, m.C,
+                            w.partial.p, w.out.p + off, 0, rs));
     off += (size_t)S * m.C;
   }
   return TNEP_OK;

@@ -101,6 +101,7 @@ struct Workspace {
   DevBuf<int> nbr_tmp, seg_R, struct_flags;
   DevBuf<float> mom;        // radial moments [slots][atom_stride]
   DevBuf<float4> pcache;    // per-pair cache of the angular walk (see FusedArgs)
+  DevBuf<int> red_offsets;  // structure offsets of the pass whose sums run on the side stream
   int mom_v0 = -1, mom_w0 = -1;
   DevBuf<float4> pos4;
   DevBuf<StructGrid> grids;
@@ -123,7 +124,7 @@ struct Workspace {
                     &types_stage, &nbr_tmp, &seg_R, &struct_flags})
       b->release();
     pos4.release(); grids.release(); boxes.release(); per_atom.release(); out.release(); partial.release();
-    mom.release(); pcache.release();
+    mom.release(); pcache.release(); red_offsets.release();
     pos_stage[0].release(); pos_stage[1].release(); box_stage.release();
     if (d_status) cudaFree(d_status);
     d_status = nullptr;
@@ -144,6 +145,11 @@ struct tnep_ctx {
   int device = 0;
   cudaStream_t stream = nullptr, copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_consumed[2] = {nullptr, nullptr};
+  // trajectories: the per-frame sums of a pass run on red_stream while the
+  // next pass's lists are built (ev_fused: the pass's fused kernels are done;
+  // ev_reduced: its sums and output copy are done)
+  cudaStream_t red_stream = nullptr;
+  cudaEvent_t ev_fused = nullptr, ev_reduced = nullptr;
   cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
   std::vector<cudaEvent_t> ev_pass;  // 3 timing events per pass, created on demand
   int n_types = 0;
@@ -202,8 +208,12 @@ tnep_status pass_events(tnep_ctx* c, int b, cudaEvent_t** ev);
 tnep_status sum_pass_times(tnep_ctx* c, int n_pass);
 // ghost: NULL, or one flag per atom of the batch (input order) marking image
 // atoms whose contributions are left out of the per-structure sums.
+// red_st: NULL, or a stream for the per-structure sums (the caller records
+// c->ev_reduced on it once it has consumed w.out); the fused kernels on st
+// first wait for the previous pass's sums (c->ev_reduced) to have read the
+// per-atom outputs.
 tnep_status run_models(tnep_ctx* c, Workspace& w, cudaStream_t st, int S, int N, cudaEvent_t ev_done,
-                       const unsigned char* ghost = nullptr);
+                       const unsigned char* ghost = nullptr, cudaStream_t red_st = nullptr);
 cudaError_t launch_zero_ghosts(int N, const int* sorted_orig, const unsigned char* ghost, float* per_atom,
                                int atom_stride, int C, cudaStream_t st);
 tnep_status check_status(tnep_ctx* c, const DevStatus& s, bool* regrow);
