@@ -131,9 +131,16 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   constexpr int NBA4 = ((NA * BA + 3) / 4) * 4;
   extern __shared__ float4 sm4[];
   float* sm = reinterpret_cast<float*>(sm4);
-  const ModelLayout& Ly = a.lay;
+  const ModelLayout& Ly = a.lay;  // the packed model (global memory)
+  // Its copy in shared memory: with the tensor cores the FP32 W0 block
+  // (nets x H x Dp floats) is left out -- the products read the BF16 tiles
+  // made from it, which are built from global memory -- and every word after
+  // it moves down by w0n.  The offsets stay expressions of the kernel
+  // parameters (no layout copy held in registers).
+  const int w0n = TC ? Ly.off_b0 - Ly.off_W0 : 0;
+  const int sm_words = Ly.words - w0n;
   const int tid = threadIdx.x;
-  float* scratch = sm + Ly.words + tid;  // slot s at scratch[s * BLK]
+  float* scratch = sm + sm_words + tid;  // slot s at scratch[s * BLK]
 
   // ---------------------------------------------------------------- tensor-core set-up (once per CTA)
   uint32_t tmem_base = 0, mbar = 0;
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   int* next_item = nullptr;  // the CTA's next work item (tensor-core path)
   if constexpr (TC) {
     constexpr int NSLOT = NA * LMAX * (LMAX + 2);
-    unsigned char* tcb = reinterpret_cast<unsigned char*>(sm + Ly.words + NSLOT * BLK);
+    unsigned char* tcb = reinterpret_cast<unsigned char*>(sm + sm_words + NSLOT * BLK);
     uint64_t* mb = reinterpret_cast<uint64_t*>(tcb);
     uint32_t* slot = reinterpret_cast<uint32_t*>(tcb + 8);
     next_item = reinterpret_cast<int*>(tcb + 16);
@@ -178,8 +185,12 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
   // loads individual `pop`'s model into shared memory (and, with the tensor
   // cores, the weight tiles made from it)
   auto load_model = [&](const int pop) {
-    const float4* src = reinterpret_cast<const float4*>(a.model + (size_t)pop * a.model_stride);
-    for (int k = tid; k < (Ly.words >> 2); k += BLK) sm4[k] = src[k];
+    const float* model = a.model + (size_t)pop * a.model_stride;
+    const float4* src = reinterpret_cast<const float4*>(model);
+    // words [0, off_W0) in place, then (tensor cores) the words after W0 moved
+    // down over it; off_W0 and off_b0 are multiples of 4
+    const int skip4 = w0n >> 2, w4 = Ly.off_W0 >> 2;
+    for (int k = tid; k < (sm_words >> 2); k += BLK) sm4[k] = src[k < w4 ? k : k + skip4];
     __syncthreads();
     if constexpr (TC) {
       // B1[net]: row = hidden unit h, column = descriptor d  (W0[h][d])
@@ -188,7 +199,7 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
       // rounding of what is left over
       for (int idx = tid; idx < Ly.nets * 32 * 32; idx += BLK) {
         const int nt = idx >> 10, r = (idx >> 5) & 31, k = idx & 31;
-        const float* W = sm + Ly.off_W0 + nt * Ly.H * DP;
+        const float* W = model + Ly.off_W0 + nt * Ly.H * DP;
         const float w1v = (r < Ly.H && k < Ly.D) ? W[r * DP + k] : 0.f;
         const float w2v = (k < Ly.H && r < Ly.D) ? W[k * DP + r] : 0.f;
         const __nv_bfloat16 h1 = __float2bfloat16_rn(w1v), h2 = __float2bfloat16_rn(w2v);
@@ -364,12 +375,12 @@ __global__ void __launch_bounds__(BLK, 256 / BLK) k_fused(const __grid_constant_
 
   // ---------------------------------------------------------------- network (Eq. 1)
   const int net = Ly.nets > 1 ? ti : 0;
-  const float* W0 = sm + Ly.off_W0 + net * Ly.H * DP;
-  const float* b0 = sm + Ly.off_b0 + net * Ly.H;
-  const float* w1 = sm + Ly.off_w1 + net * Ly.H;
-  const float* sc = sm + Ly.off_scaler;
+  const float* W0 = TC ? nullptr : sm + Ly.off_W0 + net * Ly.H * DP;  // FP32 network only
+  const float* b0 = sm + (Ly.off_b0 - w0n) + net * Ly.H;
+  const float* w1 = sm + (Ly.off_w1 - w0n) + net * Ly.H;
+  const float* sc = sm + (Ly.off_scaler - w0n);
   float e[DP];
-  float U = -sm[Ly.off_b1 + net];
+  float U = -sm[Ly.off_b1 - w0n + net];
   if constexpr (TC) {
     // z = W0 s on the tensor cores: A = s (bf16, one row per atom), B1 = W0,
     // D (F32) in TMEM columns [32 net, 32 net + 32); then e = W0^T v likewise.
@@ -881,7 +892,7 @@ size_t fused_smem_bytes(int variant, const ModelLayout& lay, int block, int tcm)
   if (variant == kVarStd) slots = 5 * 24;
   if (variant == kVarSmall) slots = 3 * 15;
   if (tc) block = 128;
-  return (size_t)(lay.words + slots * block) * sizeof(float) + (tc ? tc_smem_bytes(lay.nets) : 0);
+  return (size_t)(smem_layout(lay, tc).words + slots * block) * sizeof(float) + (tc ? tc_smem_bytes(lay.nets) : 0);
 }
 
 cudaError_t launch_fused(int variant, int rank, const FusedArgs& a, int n_pop, int block, int tcm,

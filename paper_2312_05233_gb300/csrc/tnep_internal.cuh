@@ -152,6 +152,23 @@ struct ModelLayout {
   int words;                       // total floats, multiple of 4
 };
 
+// Layout of the packed model as the fused kernel keeps it in shared memory:
+// without W0 (its FP32 block of nets x H x Dp floats, which the tensor-core
+// network does not read there) the words after it move down by that size.
+__host__ __device__ inline ModelLayout smem_layout(const ModelLayout& g, bool drop_w0) {
+  ModelLayout s = g;
+  if (drop_w0) {
+    const int w0n = g.off_b0 - g.off_W0;
+    s.off_W0 = -1;
+    s.off_b0 -= w0n;
+    s.off_w1 -= w0n;
+    s.off_b1 -= w0n;
+    s.off_scaler -= w0n;
+    s.words -= w0n;
+  }
+  return s;
+}
+
 // Arguments of the fused descriptor -> network -> partial force -> contraction kernel.
 struct FusedArgs {
   int n_atoms;
