@@ -593,7 +593,8 @@ def main():
                     help="atoms of the single-process oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=5000)
-    ap.add_argument("--serve-rates", default="100,1000,3000,5000,20000")
+    ap.add_argument("--serve-rates", default="100,300,1000,3000,5000,20000",
+                    help="Poisson arrival rates (req/s): the five of the serving workload plus a saturating one")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-population", action="store_true")
     ap.add_argument("--no-network-variants", action="store_true",
