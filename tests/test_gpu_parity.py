@@ -143,13 +143,20 @@ def test_water_small_parity(tn):
 
 
 def test_device_and_host_inputs_agree(tn):
+    """Host and device buffers give the same frames, also when the device
+    outputs of several passes are written while later passes run (the
+    per-frame sums and their copies run on a side stream)."""
     frames, types, box = synth.water_small(5)
     ms, _ = models_for(tn, 2)
     ctx = tn.tnep_create(ms, 2, RC)
     h = tn.tnep_eval(ctx, frames, box, types)
-    d = tn.tnep_eval(ctx, torch.from_numpy(frames).cuda(), torch.from_numpy(box).cuda(),
-                     torch.from_numpy(types).cuda())
+    dev = (torch.from_numpy(frames).cuda(), torch.from_numpy(box).cuda(), torch.from_numpy(types).cuda())
+    d = tn.tnep_eval(ctx, *dev)
     for a, b in zip(h, d):
+        assert np.array_equal(a, b.cpu().numpy())
+    tn.tnep_set_option(ctx, tn.TNEP_OPT_FRAMES_PER_BATCH, 2)  # three passes
+    d3 = tn.tnep_eval(ctx, *dev)
+    for a, b in zip(h, d3):
         assert np.array_equal(a, b.cpu().numpy())
     ctx.close()
 
