@@ -15,9 +15,11 @@
 // and contracts each angular partial force on the fly (Sec. II.B-C):
 //   rank 1 (Eq. 3):  mu_i    -= |r_ij|^2 dU_i/dr_ij
 //   rank 2 (Eq. 4):  alpha_i -= r_ij (x) dU_i/dr_ij,  plus U_i on the diagonal.
-// Nothing per pair is stored: angular basis values are recomputed in the
-// backward walk.  Per-atom results go out in float32 (SoA) and are summed per
-// structure in float64 by the reduce kernel.
+// With the pair cache (the default for single-model launches) the forward walk
+// stores each angular pair's r_ij, 1/|r_ij|, g_n and g_n' and the backward
+// walk reads them back; without it the backward walk recomputes them.
+// Per-atom results go out in float32 (SoA) and are summed per structure in
+// float64 by the reduce kernel.
 //
 // Angular functions: real Cartesian polynomials p_lm(u) of the unit vector u
 // with weights w_lm such that P_l(a.b) = sum_m w_lm p_lm(a) p_lm(b) (the
