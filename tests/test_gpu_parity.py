@@ -214,7 +214,12 @@ def test_small_variant_three_types(tn, per_type_nn):
 
 
 # ------------------------------------------------- uneven batch, edge cases
-def test_uneven_batch_open_and_periodic(tn):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_uneven_batch_open_and_periodic(tn, mode):
+    """Open clusters, an empty structure, a single atom, a periodic box and a
+    slab in one batch, with the network on the CUDA cores (mode 0) and on the
+    tensor cores with split-BF16 operands (mode 2, the persistent kernel),
+    both held to the FP32 bars."""
     rng = np.random.default_rng(17)
     structs = []
     for n in (5, 1, 30):
@@ -230,7 +235,7 @@ def test_uneven_batch_open_and_periodic(tn):
     structs.append(synth.Structure(p.astype(np.float32), t, np.array([12.42, 12.42, 0.0], np.float32)))
     bt = synth.concat_structures(structs)
     ms, om = models_for(tn, 2)
-    ctx = tn.tnep_create(ms, 2, RC)
+    ctx = tn.tnep_create(with_precision(tn, ms, mode, 2), 2, RC)
     outs, _ = tn.tnep_eval_batch(ctx, bt.offsets, bt.pos, bt.box, bt.types)
     for got, m in zip(outs, om):
         res = []
