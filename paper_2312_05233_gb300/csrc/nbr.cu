@@ -596,12 +596,29 @@ __global__ void __launch_bounds__(128) k_skin_compact(SkinArgs a) {
   if (bad) atomicOr(&a.status->skin_violation, 1);
   int cR = 0, cA = 0, start = 0;
   for (int t = 0; t < a.n_types; ++t) {
-    const int n = a.skin_seg[(size_t)t * a.skin_seg_stride + i];
-    const int e0 = radial_segment_start(a.skin_two_ended, t, start, n, a.skin_cap);
+    const int n_seg = a.skin_seg[(size_t)t * a.skin_seg_stride + i];
+    // entries of this type inside the row: all of them unless the skin lists
+    // overflowed, in which case the call is redone with a larger capacity and
+    // the reads only have to stay in bounds
+    const int s0 = radial_segment_start(a.skin_two_ended, t, start, n_seg, a.skin_cap);
+    const int e0 = max(s0, 0), n = max(min(s0 + n_seg, a.skin_cap) - e0, 0);
     int kept = 0;
-    for (int e = e0; e < e0 + n; ++e) {
-      const int j = a.skin_nbr[nbr_index(i, e, a.skin_cap)];
-      const float4 pj = a.pos4[base + j];
+    // Software-pipelined gather: the list index two entries ahead, the
+    // position one ahead, list rows four ahead pulled into L1 (a warp's row is
+    // one 128-byte line).  The same candidates in the same order as a plain
+    // loop over entries e0 .. e0 + n - 1; past the end the last index is
+    // re-used, so every load stays in bounds.
+    int jn = n > 0 ? a.skin_nbr[nbr_index(i, e0, a.skin_cap)] : 0;
+    int ja = n > 1 ? a.skin_nbr[nbr_index(i, e0 + 1, a.skin_cap)] : jn;
+    float4 pn = n > 0 ? a.pos4[base + jn] : pi;
+    for (int k = 0; k < n; ++k) {
+      const int j = jn;
+      const float4 pj = pn;
+      jn = ja;
+      pn = a.pos4[base + ja];
+      if (k + 2 < n) ja = a.skin_nbr[nbr_index(i, e0 + k + 2, a.skin_cap)];
+      if (k + 4 < n)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.skin_nbr + nbr_index(i, e0 + k + 4, a.skin_cap)));
       const float dx = mi_diff(pj.x, pi.x, B.L[0], B.invL[0]);
       const float dy = mi_diff(pj.y, pi.y, B.L[1], B.invL[1]);
       const float dz = mi_diff(pj.z, pi.z, B.L[2], B.invL[2]);
@@ -616,7 +633,7 @@ __global__ void __launch_bounds__(128) k_skin_compact(SkinArgs a) {
         }
       }
     }
-    start += n;
+    start += n_seg;
     a.seg_R[(size_t)t * a.seg_stride + g] = kept;
   }
   a.cnt_R[g] = cR;
