@@ -543,9 +543,12 @@ def test_dense_cluster_large_lists(tn):
     ctx.close()
 
 
-def test_population_graph_replay_and_shapes(tn):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_population_graph_replay_and_shapes(tn, mode):
     """Graph-captured generations equal the one-shot population call, for every
-    launch shape the autotuner may pick, and for new parameters each time."""
+    launch shape the autotuner may pick, and for new parameters each time;
+    with the network on the CUDA cores (mode 0) and on the tensor cores
+    (mode 2: persistent CTAs whose work counter is reset inside the graph)."""
     rng = np.random.default_rng(8)
     structs = synth.population_structures(n_clusters=10, n_boxes=4, seed_k=2)
     bt = synth.concat_structures(structs)
@@ -554,22 +557,30 @@ def test_population_graph_replay_and_shapes(tn):
     sc = synth.default_q_scaler(hp)
     target = rng.standard_normal((bt.n_structs, 9))
     params = [np.stack([synth.model_params(hp, rng) for _ in range(P)]) for _ in range(2)]
-    ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0][0], sc)], 2, RC)
+    ctx = tn.tnep_create([tn.Model.from_hyper(hp, params[0][0], sc, mlp_precision=mode)], 2, RC)
     tn.tnep_set_option(ctx, tn.TNEP_OPT_POPULATION_FORM, 1)  # per-pair walk: same arithmetic as the batch path
     pop = tn.tnep_population_create(ctx, 0, params[0], bt.offsets, bt.pos, bt.box, bt.types, target)
     info = pop.info()
     assert info["block"] in (64, 128) and info["atoms"] == len(bt.types) and info["factored"] == 0
-    assert all(t > 0 for t in info["tune_ms"][:4]) and all(t == -1 for t in info["tune_ms"][4:])
+    walk = info["tune_ms"][:4]  # (128, 64 atoms per CTA) x (structure-major, individual-major)
+    if mode == 0:
+        assert all(t > 0 for t in walk)
+    else:  # the tensor-core network takes 128-atom CTAs only
+        assert walk[0] > 0 and walk[1] > 0 and walk[2] == -1 and walk[3] == -1
+    assert all(t == -1 for t in info["tune_ms"][4:])
     for prm in params:  # two generations with different parameters
         rmse, pred = pop.eval(prm, want_out=True)
         r1, p1 = tn.tnep_eval_population(ctx, 0, prm, bt.offsets, bt.pos, bt.box, bt.types, target, want_out=True)
         np.testing.assert_allclose(pred, p1, rtol=0, atol=1e-12 * np.abs(p1).max())
         np.testing.assert_allclose(rmse, r1, rtol=1e-12)
-    c1 = tn.tnep_create([tn.Model.from_hyper(hp, params[1][0], sc)], 2, RC)
+    c1 = tn.tnep_create([tn.Model.from_hyper(hp, params[1][0], sc, mlp_precision=mode)], 2, RC)
     for block in (64, 128):  # the CTA size does not change any arithmetic
         tn.tnep_set_option(c1, tn.TNEP_OPT_BLOCK_ATOMS, block)
         (ref,), _ = tn.tnep_eval_batch(c1, bt.offsets, bt.pos, bt.box, bt.types)
-        assert np.array_equal(pred[0], ref)
+        if mode == 0:
+            assert np.array_equal(pred[0], ref)
+        else:
+            assert np.all(np.abs(pred[0] - ref) <= 1e-12 * np.abs(ref).max())
     c1.close()
     pop.close()
     ctx.close()
