@@ -421,7 +421,8 @@ tnep_status tnep_spectrum_noalloc(const double* series, int T, int C, double dt_
 enum {
   TNEP_OPT_FRAMES_PER_BATCH = 0,    /* frames per device pass in tnep_eval (0 = automatic) */
   TNEP_OPT_MAX_NEIGHBORS = 1,       /* hard cap on neighbours per atom (default 1024); lists grow up to it */
-  TNEP_OPT_BLOCK_ATOMS = 2,         /* atoms per CTA of the fused kernel: 64 or 128 (default 128) */
+  TNEP_OPT_BLOCK_ATOMS = 2,         /* atoms per CTA of the fused kernel: 64 or 128 (default 128); models whose
+                                       network runs on the tensor cores always take 128 (one per product row) */
   TNEP_OPT_LAST_KERNEL_MS = 3,      /* read-only: device time of the tensor kernels (radial moments + fused) of the last call (ms) */
   TNEP_OPT_CELL_DIV = 4,            /* cells of edge rc_R / k with a +-k stencil, k in {1, 2, 3}; stencil cells
                                        farther than the cutoff are skipped (default 1) */
